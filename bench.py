@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: spin-flip attempts per ns on one GB300 (and N GPUs
+as independent replicas).
+
+Workload (default, the 16384^2 configuration): six 16384 x 16384 periodic
+lattices, T in {1.5, 2.269185, 3.0} x {cold start, random start from seed 2};
+one step = 1000 checkerboard sweeps of all six, with E and M recorded every
+sweep.  The six lattices (192 MiB packed) are larger than L2; L2 is also
+flushed between timed steps.  Flip attempts per step = 6 * 16384^2 * 1000.
+
+Prints one JSON line (see the keys below).  --impl reference times the CPU
+oracle (the slow reference definition of the same sweep) on the host cores on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+T_RUNS = (1.5, 2.269185, 3.0)
+OPS_PER_SITE = 18.5   # algorithmic integer ops per site update (derivation in the design doc)
+SMS = 152
+INT_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=16384)
+    ap.add_argument("--sweeps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.err = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception as e:  # nvidia-smi missing
+            self.err = str(e)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": self.err or "no nvidia-smi samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+def time_oracle(L: int, seconds: float, max_sweeps: int | None = None):
+    import oracle
+    cores = os.cpu_count() or 1
+    lat = oracle.init(L, 2, 0, n_threads=cores)
+    done, t_total = 0, 0.0
+    n = 1
+    while t_total < seconds and (max_sweeps is None or done < max_sweeps):
+        if max_sweeps is not None:
+            n = min(n, max_sweeps - done)
+        t0 = time.perf_counter()
+        oracle.sweeps(lat, 2.269185, 2, 0, done, n, n_threads=cores)
+        t_total += time.perf_counter() - t0
+        done += n
+        n = min(n * 2, 64)
+    flips = done * L * L
+    return {"value": flips / (t_total * 1e9), "unit": "flip/ns", "cores": cores, "kind": "oracle",
+            "sample": f"{done} sweeps of one {L}x{L} lattice (random start seed 2, T=2.269185, E/M each "
+                      f"sweep), oracle on {cores} host threads (rows of one colour split across threads)",
+            "seconds": t_total}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        r = time_oracle(args.L, 0.0, max_sweeps=1)
+        if i >= args.warmup:
+            per_step.append(r)
+    secs = sum(r["seconds"] for r in per_step)
+    flips = len(per_step) * args.L * args.L
+    value = flips / (secs * 1e9)
+    cb = dict(per_step[0])
+    cb["value"] = value
+    cb["sample"] = f"each step: 1 sweep of one {args.L}x{args.L} lattice by the CPU oracle on {cb['cores']} threads"
+    cb.pop("seconds", None)
+    line = {"impl": "reference", "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs / len(per_step) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": f"{args.L}x{args.L} periodic lattice, checkerboard Metropolis, "
+                                   f"T=2.269185 random start (bounded sample of the six-run workload)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "flip/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def ours(args):
+    import torch
+    from paper_2404_16990_gb300 import ising
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    L, n_sw = args.L, args.sweeps
+    seed = 2 + 1000 * rank  # independent replicas per rank; rank 0 is the configured seed 2
+    sims = []
+    with torch.cuda.stream(stream):
+        for cold in (True, False):
+            s = ising.IsingSim(Ls=[L] * 3, temps=list(T_RUNS), seeds=[seed] * 3, cold=cold,
+                               trace_cap=n_sw, stream=stream, device=dev)
+            s.set_graph(True)
+            sims.append(s)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    sites = sum(sum(L * L for _ in range(3)) for _ in sims)
+    flips_per_step = sites * n_sw
+
+    def step():
+        for s in sims:
+            s.sweep(n_sw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+
+    launches0 = sum(ising.ising_kernel_launches(s.h) for s in sims)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        time.sleep(0.3)
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)            # L2 flush between timed steps
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        time.sleep(0.3)
+    launches = sum(ising.ising_kernel_launches(s.h) for s in sims) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = flips_per_step * ws / (ms_per_step * 1e6)
+
+    # dominant kernel: streaming half-sweep, 2 launches per sweep per handle
+    n_half = 2 * n_sw * len(sims) * args.steps
+    avg_launch_s = (sum(step_ms) / 1e3) / n_half
+    sites_per_launch = sites // 2 // len(sims)     # half the sites of one handle's three lattices
+    achieved = OPS_PER_SITE * sites_per_launch / avg_launch_s / 1e12
+    peak = SMS * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+    # end-to-end through the public API: host checkpoint in (pinned), sweeps,
+    # E/M traces and observables out, every step
+    e2e = None
+    if not args.no_e2e:
+        nbytes = [ising.ising_state_bytes(s.h) for s in sims]
+        host = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for nb in nbytes]
+        for s, hb, nb in zip(sims, host, nbytes):
+            ising.ising_save_to(s.h, hb.data_ptr(), nb)
+        d2h = 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            d2h = 0
+            for s, hb, nb in zip(sims, host, nbytes):
+                ising.ising_load_from(s.h, hb.data_ptr(), nb)
+                s.sweep(n_sw)
+            for s in sims:
+                E, M = s.trace(n_sw)
+                Eo, Mo = s.observables()
+                d2h += E.nbytes + M.nbytes + Eo.nbytes + Mo.nbytes
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        e2e_val = flips_per_step * args.e2e_steps / (wall * 1e9)
+        if ws > 1:
+            t = torch.tensor([wall], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = flips_per_step * ws * args.e2e_steps / (float(t.item()) * 1e9)
+        e2e = {"value": e2e_val, "unit": "flip/ns", "h2d_bytes_per_step": int(sum(nbytes)),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(L, args.cpu_seconds)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"six {L}x{L} periodic lattices, T in {{1.5, 2.269185, 3.0}} x "
+                                   f"{{cold, random seed 2}}, {n_sw} checkerboard sweeps per step, "
+                                   f"E/M recorded every sweep",
+                       "lattices_per_gpu": 6, "L": L, "sweeps_per_step": n_sw,
+                       "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps; "
+                       "working set 192 MiB > 129 MB L2", "kernel": "streaming half-sweep, CUDA graph"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "stream_half_kernel", "ops_per_site": OPS_PER_SITE,
+                         "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

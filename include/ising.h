@@ -1,0 +1,202 @@
+/*
+ * ising.h -- C ABI of libising, a GB300 (sm_103a) simulator of the 2D Ising
+ * model with checkerboard Metropolis sweeps on multi-spin-coded lattices.
+ *
+ * The model and method follow arXiv 2404.16990:
+ *   - Hamiltonian H = -J sum_<ij> s_i s_j over the four nearest neighbours of
+ *     a square periodic L x L lattice, J = 1, no field (Section 1).
+ *   - Metropolis rule, accept iff ran() < exp(-beta dE) (Section 1).
+ *   - Checkerboard order: all red/black sites ((x+y) even) in parallel, then
+ *     all blue/white sites ((x+y) odd) (Algorithm 5; Algorithm 3 is the same
+ *     loop at PE level).  One sweep attempts every spin once; the flip rate is
+ *     spins x sweeps / time (Section 3.2, Table 1).
+ *   - Many independent simulations advance at once (Section 2: one lattice
+ *     per PE column, up to 754 in Section 3.2).
+ *
+ * Definitions this library fixes where the paper leaves them open:
+ *   - Spins are stored one bit each (bit 0 = +1, bit 1 = -1), 32 per 32-bit
+ *     word, least significant bit = lowest index (the bit order of Section 2,
+ *     where 16 spins share an int16).  Lattice layout in device memory:
+ *     word[(c*L + y)*(L/64) + k] holds the sites of colour c in row y with
+ *     x = 2j + ((y+c) & 1), j = 32k + bit.  One lattice = L*L/8 bytes.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) replaces the
+ *     paper's hardware generator.  Key = (lo32(seed), hi32(seed)); counter =
+ *     (p >> 2, t, s, phase) with t the sweep index counted over the life of
+ *     the handle, s the simulation index, phase 0/1 = black/white half-sweep,
+ *     2 = random initial state; output lane p & 3.  p is the rank of the
+ *     site among the same-colour sites of its lattice in row-major order,
+ *     p = y*(L/2) + (x >> 1); for the initial state p = y*L + x.
+ *   - A site with dE <= 0 always flips; with dE in {4, 8} it flips iff
+ *     r < thr[dE/4 - 1], thr = min(floor(2^32 exp(-dE/T)), 2^32-1), computed
+ *     on the host in double precision.  Random start: s = +1 iff the top bit
+ *     of the site's phase-2 draw is 0.
+ *   - E = -sum over bonds s_i s_j and M = sum s_i are exact 64-bit integers.
+ *
+ * Conventions for every call:
+ *   - Return 0 (ISING_OK) on success, a negative ISING_E* code on failure;
+ *     ising_last_error() then gives a message (thread-local, valid until the
+ *     next failing call on the same thread).
+ *   - Device memory is owned by the caller: it passes one workspace of at
+ *     least the size the *_workspace_bytes call reports; the library never
+ *     allocates device memory and never frees the workspace.  Host arrays are
+ *     owned by the caller and read/written only during the call.
+ *   - Every device operation is issued on the CUDA stream given at creation
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).  Calls
+ *     that return host data synchronise that stream first.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - Lattice sizes: L even, 64 <= L <= 65536 and L a multiple of 64.
+ *     Temperatures: positive and finite.  Anything else is ISING_EINVAL.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISING_OK 0
+#define ISING_EINVAL (-1)    /* invalid argument */
+#define ISING_ENOMEM (-2)    /* workspace smaller than required */
+#define ISING_ECUDA (-3)     /* a CUDA call failed; see ising_last_error() */
+#define ISING_ETIMEOUT (-4)  /* a bounded device-side wait ran out */
+#define ISING_ESTATE (-5)    /* handle in a state that does not allow the call */
+
+#define ISING_INIT_RANDOM 0
+#define ISING_INIT_COLD 1
+
+#define ISING_MIN_L 64
+#define ISING_MAX_L 65536
+
+typedef struct ising_handle* ising_t;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ising_last_error(void);
+
+/* Library version string. */
+const char* ising_version(void);
+
+/* Bytes of device workspace for n_sims lattices of side L with a per-sweep
+ * E/M trace ring of trace_cap entries per lattice (0 = no trace).
+ * Errors: ISING_EINVAL for an invalid L, n_sims < 0 or trace_cap < 0. */
+int ising_workspace_bytes(int L, int n_sims, int64_t trace_cap, size_t* bytes);
+
+/* Same for a batch of lattices of possibly different sides Ls[0..n_sims-1]. */
+int ising_batch_workspace_bytes(int n_sims, const int* Ls, int64_t trace_cap, size_t* bytes);
+
+/* Create n_sims independent L x L lattices (Algorithm 5's P, one per
+ * simulation as in Algorithm 3's (gamma, beta) pairs).  temps[n_sims] are the
+ * temperatures (J = 1); seed keys every lattice's generator, simulation i
+ * uses s = i.  init = ISING_INIT_RANDOM or ISING_INIT_COLD.  dev_workspace
+ * is a device pointer (256-byte aligned) of ws_bytes >= the size reported by
+ * ising_workspace_bytes.  The initial state and its E, M are computed on
+ * cuda_stream before the call returns (asynchronously).  n_sims may be 0: the
+ * handle then does nothing.  *out receives the handle; free it with
+ * ising_destroy (the workspace stays the caller's). */
+int ising_create(ising_t* out, int L, int n_sims, const double* temps, uint64_t seed,
+                 int init, int64_t trace_cap, void* dev_workspace, size_t ws_bytes,
+                 void* cuda_stream);
+
+/* Create a batch of lattices of uneven side and temperature: lattice i has
+ * side Ls[i], temperature temps[i], key seeds[i] and simulation index s = i. */
+int ising_create_batch(ising_t* out, int n_sims, const int* Ls, const double* temps,
+                       const uint64_t* seeds, int init, int64_t trace_cap,
+                       void* dev_workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Advance every lattice by n >= 0 full sweeps (black half-sweep, then white
+ * half-sweep; Algorithm 3's loop body).  Asynchronous on the handle's stream:
+ * returns after enqueueing.  After each sweep E and M are recorded (current
+ * values, trace ring, and the FP64 moment sums if measuring is on).  If a
+ * bounded device-side wait of the resident kernel runs out, the next call that
+ * synchronises returns ISING_ETIMEOUT and the state is undefined.  The sweep
+ * counter must stay below 2^32 (ISING_EINVAL otherwise). */
+int ising_sweep(ising_t h, int64_t n);
+
+/* Sweeps done since creation (the t of the next sweep). */
+int64_t ising_sweeps_done(ising_t h);
+
+/* Kernels this handle has enqueued so far (each CUDA-graph replay counts the
+ * kernels of the graph); -1 for a NULL handle.  A diagnostic for profiling. */
+int64_t ising_kernel_launches(ising_t h);
+
+/* Current E[n_sims], M[n_sims] (host arrays, caller-owned).  Synchronises. */
+int ising_observables(ising_t h, int64_t* E, int64_t* M);
+
+/* The last n = min(sweeps recorded, trace_cap, max_sweeps) trace entries of
+ * every lattice, oldest first: E[i*n + j], M[i*n + j] for lattice i.  *n_out
+ * receives n.  Synchronises. */
+int ising_trace(ising_t h, int64_t* E, int64_t* M, int64_t max_sweeps, int64_t* n_out);
+
+/* Unpacked spins (+1/-1, row-major L x L) of lattice sim.  Synchronises. */
+int ising_get_spins(ising_t h, int sim, int8_t* host_LxL);
+
+/* Overwrite lattice sim with host spins (+1/-1; any other value is
+ * ISING_EINVAL); its E and M are recomputed on the device. */
+int ising_set_spins(ising_t h, int sim, const int8_t* host_LxL);
+
+/* Device address and length (in 32-bit words, L*L/32) of the packed spins of
+ * lattice sim, in the layout described at the top of this file.  The memory
+ * belongs to the caller's workspace; reading it is safe once the handle's
+ * stream has finished the sweeps that write it. */
+int ising_lattice_words(ising_t h, int sim, void** dev_words, size_t* n_words);
+
+/* The acceptance thresholds thr[2*i], thr[2*i+1] (dE = 4, 8) of every lattice. */
+int ising_get_thresholds(ising_t h, uint32_t* thr);
+
+/* Lattice side of simulation sim (0 if out of range). */
+int ising_lattice_size(ising_t h, int sim);
+
+/* Number of simulations of the handle. */
+int ising_num_sims(ising_t h);
+
+/* Turn the accumulation of FP64 moments on (1) or off (0). */
+int ising_set_measure(ising_t h, int on);
+
+/* Zero the moment sums. */
+int ising_reset_moments(ising_t h);
+
+/* Moment sums of every lattice over the measured sweeps, 6 doubles each:
+ * out[6*i + 0..5] = count, sum |m|, sum m^2, sum m^4, sum e, sum e^2 with
+ * m = M/L^2 and e = E/L^2.  Synchronises. */
+int ising_moments(ising_t h, double* out);
+
+/* Size of a checkpoint of the handle (spins, sweep counter, current E/M,
+ * moment sums), and save/load through a host buffer of that size.  Loading
+ * into a handle of a different shape is ISING_EINVAL.  Because the generator
+ * is counter-based, n sweeps, save, load, m sweeps give the same bits as
+ * n + m sweeps. */
+int ising_state_bytes(ising_t h, size_t* bytes);
+int ising_save(ising_t h, void* host_buf, size_t bytes);
+int ising_load(ising_t h, const void* host_buf, size_t bytes);
+
+/* Execution plan.  ISING_PLAN_AUTO picks the kernel from the lattice sizes
+ * (lattices up to L = 1024 stay resident, larger ones stream); the others
+ * force one kernel for every lattice: RESIDENT keeps each lattice (or group
+ * of equal-size lattices) in shared memory for many sweeps (up to the
+ * shared-memory limit, else ISING_EINVAL); STREAM runs one launch per
+ * half-sweep over the lattices in device memory.  Tuning knobs (0 = default):
+ * words_per_thread in {1, 2, 4} = 32-bit words per streaming thread and row;
+ * rows_per_item = rows per streaming thread; sweeps_per_unit = sweeps a
+ * resident work unit runs before its group is stored; threads = block size
+ * (a multiple of 32, at most 1024 resident / 256 streaming).  No choice
+ * changes any result bit. */
+#define ISING_PLAN_AUTO 0
+#define ISING_PLAN_RESIDENT 1
+#define ISING_PLAN_STREAM 2
+int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
+                   int sweeps_per_unit, int threads);
+
+/* Replay the sweeps of each later ising_sweep(h, n) call through a CUDA graph
+ * captured for that n (1 = on, 0 = off).  Results are identical either way. */
+int ising_set_graph(ising_t h, int on);
+
+/* Free the handle (not the workspace).  Synchronises its stream. */
+void ising_destroy(ising_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

@@ -1,0 +1,763 @@
+// ising_api.cu -- host side of the C ABI declared in include/ising.h.
+//
+// Owns no device memory: every device array lives in the caller's workspace,
+// carved up by compute_layout().  Kernels are in ising_kernels.cu.
+#include "../../include/ising.h"
+#include "ising_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace ising;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(ISING_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                          \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxGroup = 256;            // lattices per resident group (matches the kernel)
+constexpr uint32_t kSaveMagic = 0x49534E47u;  // "ISNG"
+constexpr uint32_t kSaveVersion = 1;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_L(int L) { return L >= ISING_MIN_L && L <= ISING_MAX_L && (L % 64) == 0; }
+
+// thr = min(floor(2^32 exp(-dE/T)), 2^32 - 1) in double precision.
+uint32_t threshold_u32(double dE, double T) {
+    const double v = std::ldexp(std::exp(-dE / T), 32);
+    if (v >= 4294967296.0) return 0xFFFFFFFFu;
+    return (uint32_t)std::floor(v);
+}
+
+struct Layout {
+    size_t lat = 0, groups = 0, members = 0, slats = 0, done = 0, acc = 0, obs = 0, trace = 0,
+           mom = 0, ctl = 0, list = 0, spins = 0, total = 0;
+    std::vector<uint64_t> word_off;  // per lattice, in 32-bit words from `spins`
+    size_t spin_bytes = 0;
+};
+
+bool compute_layout(int n, const int* Ls, int64_t trace_cap, Layout* out) {
+    Layout l;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t nn = (size_t)n;
+    l.ctl = take(sizeof(Control));
+    l.lat = take(nn * sizeof(LatDesc));
+    l.groups = take(nn * sizeof(GroupDesc));
+    l.members = take(nn * sizeof(uint32_t));
+    l.slats = take(nn * sizeof(StreamLat));
+    l.done = take(nn * sizeof(unsigned int));
+    l.acc = take(nn * 2 * sizeof(unsigned long long));
+    l.obs = take(nn * 2 * sizeof(long long));
+    if (trace_cap > 0 && nn > 0 && (size_t)trace_cap > (SIZE_MAX / 32) / nn) return false;
+    l.trace = take(nn * (size_t)trace_cap * 2 * sizeof(long long));
+    l.mom = take(nn * 6 * sizeof(double));
+    l.list = take(nn * sizeof(uint32_t));
+    l.spins = off;
+    uint64_t words = 0;
+    l.word_off.resize(nn);
+    for (int i = 0; i < n; ++i) {
+        l.word_off[i] = words;
+        words += (uint64_t)Ls[i] * (uint64_t)Ls[i] / 32;  // L*L/8 bytes
+    }
+    l.spin_bytes = (size_t)words * 4;
+    off = align_up(off + l.spin_bytes);
+    l.total = off;
+    *out = l;
+    return true;
+}
+
+struct Plan {
+    int mode = ISING_PLAN_AUTO;
+    int words_per_thread = 0;   // stream: V (0 = default)
+    int rows_per_item = 4;      // stream: R
+    int stream_threads = 256;
+    int sweeps_per_unit = 0;    // resident: k (0 = default)
+    int resident_threads = 0;   // 0 = from group size
+};
+
+}  // namespace
+
+struct ising_handle {
+    int n = 0;
+    std::vector<int> L;
+    std::vector<double> T;
+    std::vector<uint64_t> seed;
+    std::vector<uint32_t> thr;
+    int64_t trace_cap = 0;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout layout;
+    DevState st{};
+    int64_t t = 0;
+    int measure = 0;
+    Plan plan;
+    bool graph = false;
+    std::map<int64_t, cudaGraphExec_t> graphs;
+    // resolved execution tables
+    bool tables_ready = false;
+    int n_groups = 0;
+    size_t group_smem = 0;
+    int res_threads = 0;
+    int res_grid = 0;
+    int n_slats = 0;
+    uint64_t total_tiles = 0;
+    int V = 1;
+    int stream_grid = 0;
+    int sms = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void drop_graphs(ising_handle* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+int check_device_error(ising_handle* h) {
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, &h->st.ctl->error, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+             "read error flag");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    if (err != 0)
+        return fail(ISING_ETIMEOUT, "a bounded device wait of the resident kernel ran out (flag %d)", err);
+    return ISING_OK;
+}
+
+// Build the resident groups and streamed lattice tables for the current plan
+// and upload them (asynchronously, from host buffers kept alive by a sync).
+int build_tables(ising_handle* h) {
+    const int n = h->n;
+    h->sms = device_sm_count();
+    const size_t optin = device_max_smem_optin();
+    const size_t static_smem = 16 * 1024;  // SiteKey/lattice tables and counters of the kernel
+    const size_t res_budget = optin > static_smem ? optin - static_smem : 0;
+    std::vector<int> resident, streamed;
+    for (int i = 0; i < n; ++i) {
+        const size_t bytes = (size_t)h->L[i] * h->L[i] / 8;
+        bool res;
+        if (h->plan.mode == ISING_PLAN_RESIDENT) {
+            if (bytes > res_budget)
+                return fail(ISING_EINVAL, "lattice %d (L=%d) does not fit in shared memory (%zu > %zu bytes)",
+                            i, h->L[i], bytes, res_budget);
+            res = true;
+        } else if (h->plan.mode == ISING_PLAN_STREAM) {
+            res = false;
+        } else {
+            res = h->L[i] <= 1024 && bytes <= res_budget;
+        }
+        (res ? resident : streamed).push_back(i);
+    }
+
+    // resident groups: equal L, filled up to the shared-memory budget, then
+    // split so that there are at least as many groups as SMs when possible
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> members;
+    h->group_smem = 0;
+    if (!resident.empty()) {
+        std::stable_sort(resident.begin(), resident.end(), [&](int a, int b) { return h->L[a] < h->L[b]; });
+        double total_sites = 0;
+        for (int i : resident) total_sites += (double)h->L[i] * h->L[i];
+        size_t i0 = 0;
+        int full_groups = 0;
+        std::vector<std::pair<size_t, size_t>> classes;  // [begin, end) of equal L
+        while (i0 < resident.size()) {
+            size_t i1 = i0;
+            while (i1 < resident.size() && h->L[resident[i1]] == h->L[resident[i0]]) ++i1;
+            classes.push_back({i0, i1});
+            const size_t bytes = (size_t)h->L[resident[i0]] * h->L[resident[i0]] / 8;
+            const size_t maxg = std::min<size_t>(kMaxGroup, std::max<size_t>(1, res_budget / bytes));
+            full_groups += (int)((i1 - i0 + maxg - 1) / maxg);
+            i0 = i1;
+        }
+        for (auto [b, e] : classes) {
+            const int Lc = h->L[resident[b]];
+            const size_t bytes = (size_t)Lc * Lc / 8;
+            size_t per = std::min<size_t>(kMaxGroup, std::max<size_t>(1, res_budget / bytes));
+            const size_t cnt = e - b;
+            if (full_groups < h->sms) {
+                // spread this class over its share of the SMs
+                const double share = (double)cnt * Lc * Lc / total_sites;
+                const size_t want = std::max<size_t>(1, (size_t)std::floor(share * h->sms));
+                per = std::min(per, std::max<size_t>(1, (cnt + want - 1) / want));
+            }
+            for (size_t j = b; j < e; j += per) {
+                const size_t c = std::min(per, e - j);
+                GroupDesc g{};
+                g.member_off = (uint32_t)members.size();
+                g.count = (uint32_t)c;
+                g.L = (uint32_t)Lc;
+                g.wn = (uint32_t)(Lc / 64);
+                for (size_t q = j; q < j + c; ++q) members.push_back((uint32_t)resident[q]);
+                groups.push_back(g);
+                h->group_smem = std::max(h->group_smem, c * bytes);
+            }
+        }
+    }
+    h->n_groups = (int)groups.size();
+    if (h->n_groups > 0) {
+        size_t max_words = 0;
+        for (auto& g : groups) max_words = std::max(max_words, (size_t)g.count * g.L * g.wn);
+        int thr = h->plan.resident_threads;
+        if (thr <= 0) thr = (int)std::min<size_t>(1024, std::max<size_t>(64, (max_words + 31) / 32 * 32));
+        h->res_threads = thr;
+        const int occ = resident_occupancy(thr, h->group_smem);
+        if (occ <= 0)
+            return fail(ISING_EINVAL, "resident kernel cannot launch with %d threads and %zu bytes of shared memory",
+                        thr, h->group_smem);
+        h->res_grid = std::min(h->n_groups, h->sms * occ);
+    }
+
+    // streamed lattices: tiles of (tw word groups) x (th row groups of R rows)
+    std::vector<StreamLat> slats;
+    int V = h->plan.words_per_thread > 0 ? h->plan.words_per_thread : 2;
+    for (int i : streamed)
+        while (V > 1 && (h->L[i] / 64) % V != 0) V /= 2;
+    h->V = V;
+    const int R = std::max(1, h->plan.rows_per_item);
+    const int B = h->plan.stream_threads;
+    uint64_t tiles = 0;
+    for (int i : streamed) {
+        StreamLat s{};
+        s.lat = (uint32_t)i;
+        const uint32_t wn = (uint32_t)(h->L[i] / 64);
+        s.groups = wn / (uint32_t)V;
+        const uint32_t tw = std::min<uint32_t>(s.groups, (uint32_t)B);
+        const uint32_t th = (uint32_t)B / tw;
+        const uint32_t tiles_x = (s.groups + tw - 1) / tw;
+        const uint32_t tiles_y = ((uint32_t)h->L[i] + th * R - 1) / (th * R);
+        s.strips = tiles_y;
+        s.item_begin = tiles;
+        tiles += (uint64_t)tiles_x * tiles_y;
+        slats.push_back(s);
+    }
+    h->n_slats = (int)slats.size();
+    h->total_tiles = tiles;
+    if (h->n_slats > 0) {
+        const int occ = stream_occupancy(V, B);
+        if (occ <= 0) return fail(ISING_EINVAL, "streaming kernel cannot launch with %d threads", B);
+        h->stream_grid = (int)std::min<uint64_t>(tiles, (uint64_t)h->sms * occ);
+    }
+
+    if (!groups.empty())
+        CUDA_TRY(cudaMemcpyAsync(h->ws + h->layout.groups, groups.data(), groups.size() * sizeof(GroupDesc),
+                                 cudaMemcpyHostToDevice, h->stream), "upload groups");
+    if (!members.empty())
+        CUDA_TRY(cudaMemcpyAsync(h->ws + h->layout.members, members.data(), members.size() * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, h->stream), "upload members");
+    if (!slats.empty())
+        CUDA_TRY(cudaMemcpyAsync(h->ws + h->layout.slats, slats.data(), slats.size() * sizeof(StreamLat),
+                                 cudaMemcpyHostToDevice, h->stream), "upload stream tables");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize after table upload");
+    h->tables_ready = true;
+    drop_graphs(h);
+    return ISING_OK;
+}
+
+// Kernels one enqueue_sweeps(h, n) issues.
+int64_t kernels_per_call(const ising_handle* h, int64_t n) {
+    int64_t k = 0;
+    if (h->n_groups > 0) k += 1;
+    if (h->n_slats > 0) k += 2 * n;
+    else if (h->n_groups > 0) k += 1;
+    return k;
+}
+
+int enqueue_sweeps(ising_handle* h, int64_t n) {
+    if (h->n_groups > 0) {
+        CUDA_TRY(cudaMemsetAsync(&h->st.ctl->ticket, 0, sizeof(unsigned int), h->stream), "reset tickets");
+        CUDA_TRY(cudaMemsetAsync(h->st.done, 0, (size_t)h->n_groups * sizeof(unsigned int), h->stream),
+                 "reset chunk flags");
+        int k = h->plan.sweeps_per_unit;
+        if (k <= 0) k = (int)std::min<int64_t>(n, 64);
+        CUDA_TRY(launch_resident(h->st, h->n_groups, n, k, h->res_threads, h->res_grid, h->group_smem,
+                                 h->stream), "resident kernel launch");
+    }
+    if (h->n_slats > 0) {
+        CUDA_TRY(launch_stream_sweeps(h->st, h->n_slats, h->total_tiles, h->V, std::max(1, h->plan.rows_per_item),
+                                      h->plan.stream_threads, h->stream_grid, n, h->stream),
+                 "streaming kernel launch");
+    } else if (h->n_groups > 0) {
+        CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
+    }
+    return ISING_OK;
+}
+
+int create_common(ising_t* out, int n, const int* Ls, const double* temps, const uint64_t* seeds,
+                  uint64_t one_seed, int init, int64_t trace_cap, void* ws, size_t ws_bytes,
+                  void* stream) {
+    if (!out) return fail(ISING_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(ISING_EINVAL, "n_sims must be >= 0 (got %d)", n);
+    if (trace_cap < 0) return fail(ISING_EINVAL, "trace_cap must be >= 0");
+    if (init != ISING_INIT_RANDOM && init != ISING_INIT_COLD) return fail(ISING_EINVAL, "init must be 0 or 1");
+    if (n > 0 && (!Ls || !temps)) return fail(ISING_EINVAL, "Ls/temps is NULL");
+    for (int i = 0; i < n; ++i) {
+        if (!valid_L(Ls[i]))
+            return fail(ISING_EINVAL, "lattice %d: L=%d must be a multiple of 64 in [%d, %d]", i, Ls[i],
+                        ISING_MIN_L, ISING_MAX_L);
+        if (!(temps[i] > 0.0) || !std::isfinite(temps[i]))
+            return fail(ISING_EINVAL, "lattice %d: temperature must be positive and finite", i);
+    }
+    Layout lay;
+    if (!compute_layout(n, Ls, trace_cap, &lay)) return fail(ISING_EINVAL, "trace_cap too large");
+    if (ws_bytes < lay.total)
+        return fail(ISING_ENOMEM, "workspace too small: %zu bytes given, %zu needed", ws_bytes, lay.total);
+    if (!ws) return fail(ISING_EINVAL, "workspace is NULL");
+    if (((uintptr_t)ws) % kAlign != 0) return fail(ISING_EINVAL, "workspace must be 256-byte aligned");
+
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaPointerAttributes attr{};
+    CUDA_TRY(cudaPointerGetAttributes(&attr, ws), "cudaPointerGetAttributes");
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(ISING_EINVAL, "workspace is not device memory");
+    CUDA_TRY(configure_kernels(), "configure kernels");
+
+    auto* h = new ising_handle();
+    h->n = n;
+    h->L.assign(Ls, Ls + n);
+    h->T.assign(temps, temps + n);
+    h->seed.resize(n);
+    for (int i = 0; i < n; ++i) h->seed[i] = seeds ? seeds[i] : one_seed;
+    h->thr.resize(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        h->thr[2 * i] = threshold_u32(4.0, temps[i]);
+        h->thr[2 * i + 1] = threshold_u32(8.0, temps[i]);
+    }
+    h->trace_cap = trace_cap;
+    h->stream = (cudaStream_t)stream;
+    h->ws = (char*)ws;
+    h->ws_bytes = ws_bytes;
+    h->layout = lay;
+    DevState& st = h->st;
+    st.ctl = (Control*)(h->ws + lay.ctl);
+    st.lat = (const LatDesc*)(h->ws + lay.lat);
+    st.groups = (const GroupDesc*)(h->ws + lay.groups);
+    st.members = (const uint32_t*)(h->ws + lay.members);
+    st.slats = (const StreamLat*)(h->ws + lay.slats);
+    st.done = (unsigned int*)(h->ws + lay.done);
+    st.acc = (unsigned long long*)(h->ws + lay.acc);
+    st.obs = (long long*)(h->ws + lay.obs);
+    st.trace = (long long*)(h->ws + lay.trace);
+    st.mom = (double*)(h->ws + lay.mom);
+    st.spins = (uint32_t*)(h->ws + lay.spins);
+    st.n = n;
+
+    std::vector<LatDesc> descs(n);
+    for (int i = 0; i < n; ++i) {
+        LatDesc d{};
+        d.word_off = lay.word_off[i];
+        d.L = (uint32_t)Ls[i];
+        d.wn = (uint32_t)(Ls[i] / 64);
+        d.sim = (uint32_t)i;
+        d.key0 = (uint32_t)(h->seed[i] & 0xFFFFFFFFull);
+        d.key1 = (uint32_t)(h->seed[i] >> 32);
+        d.thr0 = h->thr[2 * i];
+        d.thr1 = h->thr[2 * i + 1];
+        descs[i] = d;
+    }
+    std::vector<uint32_t> list(n);
+    std::iota(list.begin(), list.end(), 0u);
+    Control ctl{};
+    ctl.trace_cap = trace_cap;
+
+    auto cleanup = [&](int rc) { delete h; return rc; };
+    // zero everything except the spin array, then fill tables
+    cudaError_t e = cudaMemsetAsync(h->ws, 0, lay.spins, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ws + lay.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(h->ws + lay.lat, descs.data(), n * sizeof(LatDesc), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(h->ws + lay.list, list.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && n > 0) {
+        if (init == ISING_INIT_COLD)
+            e = cudaMemsetAsync(h->ws + lay.spins, 0, lay.spin_bytes, h->stream);
+        else
+            e = launch_init_random(st, n, h->stream);
+    }
+    if (e == cudaSuccess && n > 0)
+        e = launch_observables(st, n, (const uint32_t*)(h->ws + lay.list), n, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host buffers above go out of scope
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "create"));
+    int rc = build_tables(h);
+    if (rc != ISING_OK) return cleanup(rc);
+    *out = h;
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ising_last_error(void) { return g_last_error.c_str(); }
+
+const char* ising_version(void) { return "libising 0.1 (sm_103a)"; }
+
+int ising_workspace_bytes(int L, int n_sims, int64_t trace_cap, size_t* bytes) {
+    if (!bytes) return fail(ISING_EINVAL, "bytes is NULL");
+    if (!valid_L(L)) return fail(ISING_EINVAL, "L=%d must be a multiple of 64 in [%d, %d]", L, ISING_MIN_L, ISING_MAX_L);
+    if (n_sims < 0 || trace_cap < 0) return fail(ISING_EINVAL, "n_sims and trace_cap must be >= 0");
+    std::vector<int> Ls((size_t)n_sims, L);
+    Layout l;
+    if (!compute_layout(n_sims, Ls.data(), trace_cap, &l)) return fail(ISING_EINVAL, "trace_cap too large");
+    *bytes = l.total;
+    return ISING_OK;
+}
+
+int ising_batch_workspace_bytes(int n_sims, const int* Ls, int64_t trace_cap, size_t* bytes) {
+    if (!bytes) return fail(ISING_EINVAL, "bytes is NULL");
+    if (n_sims < 0 || trace_cap < 0) return fail(ISING_EINVAL, "n_sims and trace_cap must be >= 0");
+    if (n_sims > 0 && !Ls) return fail(ISING_EINVAL, "Ls is NULL");
+    for (int i = 0; i < n_sims; ++i)
+        if (!valid_L(Ls[i])) return fail(ISING_EINVAL, "lattice %d: L=%d invalid", i, Ls[i]);
+    Layout l;
+    if (!compute_layout(n_sims, Ls, trace_cap, &l)) return fail(ISING_EINVAL, "trace_cap too large");
+    *bytes = l.total;
+    return ISING_OK;
+}
+
+int ising_create(ising_t* out, int L, int n_sims, const double* temps, uint64_t seed, int init,
+                 int64_t trace_cap, void* dev_workspace, size_t ws_bytes, void* cuda_stream) {
+    if (n_sims > 0 && !valid_L(L))
+        return fail(ISING_EINVAL, "L=%d must be a multiple of 64 in [%d, %d]", L, ISING_MIN_L, ISING_MAX_L);
+    if (n_sims < 0) return fail(ISING_EINVAL, "n_sims must be >= 0");
+    std::vector<int> Ls((size_t)n_sims, L);
+    return create_common(out, n_sims, Ls.data(), temps, nullptr, seed, init, trace_cap, dev_workspace,
+                         ws_bytes, cuda_stream);
+}
+
+int ising_create_batch(ising_t* out, int n_sims, const int* Ls, const double* temps, const uint64_t* seeds,
+                       int init, int64_t trace_cap, void* dev_workspace, size_t ws_bytes, void* cuda_stream) {
+    if (n_sims > 0 && !seeds) return fail(ISING_EINVAL, "seeds is NULL");
+    return create_common(out, n_sims, Ls, temps, seeds, 0, init, trace_cap, dev_workspace, ws_bytes, cuda_stream);
+}
+
+int ising_sweep(ising_t h, int64_t n) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
+    if (n == 0 || h->n == 0) return ISING_OK;
+    if (h->t + n > (int64_t)0xFFFFFFFFll)
+        return fail(ISING_EINVAL, "sweep counter would pass 2^32 (Philox counter word 1)");
+    if (!h->tables_ready) {
+        int rc = build_tables(h);
+        if (rc != ISING_OK) return rc;
+    }
+    if (h->n_groups > 0) {
+        int k = h->plan.sweeps_per_unit > 0 ? h->plan.sweeps_per_unit : (int)std::min<int64_t>(n, 64);
+        const int64_t tickets = ((n + k - 1) / k) * (int64_t)h->n_groups;
+        if (tickets >= (int64_t)0x7FFFFFFF) return fail(ISING_EINVAL, "too many work units; call ising_sweep with fewer sweeps");
+    }
+    if (h->graph) {
+        if (h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");
+        auto it = h->graphs.find(n);
+        if (it == h->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            int rc = enqueue_sweeps(h, n);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (rc != ISING_OK) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            it = h->graphs.emplace(n, ex).first;
+        }
+        CUDA_TRY(cudaGraphLaunch(it->second, h->stream), "graph launch");
+    } else {
+        int rc = enqueue_sweeps(h, n);
+        if (rc != ISING_OK) return rc;
+    }
+    h->t += n;
+    h->launches += kernels_per_call(h, n);
+    return ISING_OK;
+}
+
+int64_t ising_sweeps_done(ising_t h) { return h ? h->t : -1; }
+
+int64_t ising_kernel_launches(ising_t h) { return h ? h->launches : -1; }
+
+int ising_num_sims(ising_t h) { return h ? h->n : 0; }
+
+int ising_lattice_size(ising_t h, int sim) {
+    if (!h || sim < 0 || sim >= h->n) return 0;
+    return h->L[sim];
+}
+
+int ising_observables(ising_t h, int64_t* E, int64_t* M) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (h->n == 0) return ISING_OK;
+    if (!E || !M) return fail(ISING_EINVAL, "E/M is NULL");
+    std::vector<long long> buf(2 * (size_t)h->n);
+    CUDA_TRY(cudaMemcpyAsync(buf.data(), h->st.obs, buf.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream),
+             "copy observables");
+    int rc = check_device_error(h);
+    if (rc != ISING_OK) return rc;
+    for (int i = 0; i < h->n; ++i) { E[i] = buf[2 * i]; M[i] = buf[2 * i + 1]; }
+    return ISING_OK;
+}
+
+int ising_trace(ising_t h, int64_t* E, int64_t* M, int64_t max_sweeps, int64_t* n_out) {
+    if (!h || !n_out) return fail(ISING_EINVAL, "handle or n_out is NULL");
+    *n_out = 0;
+    if (max_sweeps < 0) return fail(ISING_EINVAL, "max_sweeps must be >= 0");
+    const int64_t cap = h->trace_cap;
+    const int64_t k = std::min(std::min(h->t, cap), max_sweeps);
+    if (h->n == 0 || k == 0) { *n_out = 0; return ISING_OK; }
+    if (!E || !M) return fail(ISING_EINVAL, "E/M is NULL");
+    std::vector<long long> buf((size_t)h->n * cap * 2);
+    CUDA_TRY(cudaMemcpyAsync(buf.data(), h->st.trace, buf.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+                             h->stream), "copy trace");
+    int rc = check_device_error(h);
+    if (rc != ISING_OK) return rc;
+    for (int i = 0; i < h->n; ++i)
+        for (int64_t j = 0; j < k; ++j) {
+            const int64_t t = h->t - k + j;
+            const int64_t slot = t % cap;
+            E[(size_t)i * k + j] = buf[((size_t)i * cap + slot) * 2];
+            M[(size_t)i * k + j] = buf[((size_t)i * cap + slot) * 2 + 1];
+        }
+    *n_out = k;
+    return ISING_OK;
+}
+
+int ising_get_spins(ising_t h, int sim, int8_t* out) {
+    if (!h || !out) return fail(ISING_EINVAL, "handle or buffer is NULL");
+    if (sim < 0 || sim >= h->n) return fail(ISING_EINVAL, "sim %d out of range", sim);
+    const int L = h->L[sim];
+    const size_t wn = (size_t)L / 64;
+    std::vector<uint32_t> w((size_t)L * L / 32);
+    CUDA_TRY(cudaMemcpyAsync(w.data(), h->st.spins + h->layout.word_off[sim], w.size() * 4,
+                             cudaMemcpyDeviceToHost, h->stream), "copy spins");
+    int rc = check_device_error(h);
+    if (rc != ISING_OK) return rc;
+    for (int c = 0; c < 2; ++c)
+        for (int y = 0; y < L; ++y)
+            for (size_t k = 0; k < wn; ++k) {
+                const uint32_t word = w[((size_t)c * L + y) * wn + k];
+                for (int b = 0; b < 32; ++b) {
+                    const size_t x = 2 * (32 * k + b) + ((y + c) & 1);
+                    out[(size_t)y * L + x] = ((word >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
+                }
+            }
+    return ISING_OK;
+}
+
+int ising_set_spins(ising_t h, int sim, const int8_t* in) {
+    if (!h || !in) return fail(ISING_EINVAL, "handle or buffer is NULL");
+    if (sim < 0 || sim >= h->n) return fail(ISING_EINVAL, "sim %d out of range", sim);
+    const int L = h->L[sim];
+    const size_t wn = (size_t)L / 64;
+    std::vector<uint32_t> w((size_t)L * L / 32, 0u);
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            const int8_t v = in[(size_t)y * L + x];
+            if (v != 1 && v != -1) return fail(ISING_EINVAL, "spin (%d,%d) is %d, not +1/-1", x, y, (int)v);
+            const int c = (x + y) & 1;
+            const size_t j = (size_t)x >> 1, k = j / 32, b = j % 32;
+            if (v == -1) w[((size_t)c * L + y) * wn + k] |= 1u << b;
+        }
+    CUDA_TRY(cudaMemcpyAsync(h->st.spins + h->layout.word_off[sim], w.data(), w.size() * 4, cudaMemcpyHostToDevice,
+                             h->stream), "copy spins");
+    CUDA_TRY(launch_observables(h->st, h->n, (const uint32_t*)(h->ws + h->layout.list) + sim, 1, h->stream),
+             "observables");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_lattice_words(ising_t h, int sim, void** dev_words, size_t* n_words) {
+    if (!h || !dev_words || !n_words) return fail(ISING_EINVAL, "NULL argument");
+    if (sim < 0 || sim >= h->n) return fail(ISING_EINVAL, "sim %d out of range", sim);
+    *dev_words = (void*)(h->st.spins + h->layout.word_off[sim]);
+    *n_words = (size_t)h->L[sim] * h->L[sim] / 32;
+    return ISING_OK;
+}
+
+int ising_get_thresholds(ising_t h, uint32_t* thr) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (h->n == 0) return ISING_OK;
+    if (!thr) return fail(ISING_EINVAL, "thr is NULL");
+    std::copy(h->thr.begin(), h->thr.end(), thr);
+    return ISING_OK;
+}
+
+int ising_set_measure(ising_t h, int on) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    h->measure = on ? 1 : 0;
+    CUDA_TRY(cudaMemcpyAsync(&h->st.ctl->measure, &h->measure, sizeof(int), cudaMemcpyHostToDevice, h->stream),
+             "set measure");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_reset_moments(ising_t h) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (h->n == 0) return ISING_OK;
+    CUDA_TRY(cudaMemsetAsync(h->st.mom, 0, (size_t)h->n * 6 * sizeof(double), h->stream), "reset moments");
+    return ISING_OK;
+}
+
+int ising_moments(ising_t h, double* out) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (h->n == 0) return ISING_OK;
+    if (!out) return fail(ISING_EINVAL, "out is NULL");
+    CUDA_TRY(cudaMemcpyAsync(out, h->st.mom, (size_t)h->n * 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "copy moments");
+    return check_device_error(h);
+}
+
+namespace {
+struct SaveHeader {
+    uint32_t magic, version;
+    int32_t n;
+    int32_t pad;
+    int64_t t;
+    uint64_t spin_bytes;
+};
+}  // namespace
+
+int ising_state_bytes(ising_t h, size_t* bytes) {
+    if (!h || !bytes) return fail(ISING_EINVAL, "handle or bytes is NULL");
+    *bytes = sizeof(SaveHeader) + (size_t)h->n * sizeof(int32_t) + h->layout.spin_bytes +
+             (size_t)h->n * 2 * sizeof(long long) + (size_t)h->n * 6 * sizeof(double);
+    return ISING_OK;
+}
+
+int ising_save(ising_t h, void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = ising_state_bytes(h, &need);
+    if (rc != ISING_OK) return rc;
+    if (!buf || bytes < need) return fail(ISING_EINVAL, "buffer too small (%zu < %zu)", bytes, need);
+    char* p = (char*)buf;
+    SaveHeader hd{kSaveMagic, kSaveVersion, h->n, 0, h->t, h->layout.spin_bytes};
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    for (int i = 0; i < h->n; ++i) { int32_t L = h->L[i]; memcpy(p, &L, 4); p += 4; }
+    if (h->n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(p, h->st.spins, h->layout.spin_bytes, cudaMemcpyDeviceToHost, h->stream), "save spins");
+        p += h->layout.spin_bytes;
+        CUDA_TRY(cudaMemcpyAsync(p, h->st.obs, (size_t)h->n * 2 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream),
+                 "save observables");
+        p += (size_t)h->n * 2 * sizeof(long long);
+        CUDA_TRY(cudaMemcpyAsync(p, h->st.mom, (size_t)h->n * 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "save moments");
+    }
+    return check_device_error(h);
+}
+
+int ising_load(ising_t h, const void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = ising_state_bytes(h, &need);
+    if (rc != ISING_OK) return rc;
+    if (!buf || bytes < need) return fail(ISING_EINVAL, "buffer too small (%zu < %zu)", bytes, need);
+    const char* p = (const char*)buf;
+    SaveHeader hd;
+    memcpy(&hd, p, sizeof(hd));
+    p += sizeof(hd);
+    if (hd.magic != kSaveMagic || hd.version != kSaveVersion) return fail(ISING_EINVAL, "not an ising checkpoint");
+    if (hd.n != h->n || hd.spin_bytes != h->layout.spin_bytes) return fail(ISING_EINVAL, "checkpoint shape differs");
+    for (int i = 0; i < h->n; ++i) {
+        int32_t L;
+        memcpy(&L, p, 4);
+        p += 4;
+        if (L != h->L[i]) return fail(ISING_EINVAL, "checkpoint lattice %d has L=%d, handle has %d", i, L, h->L[i]);
+    }
+    if (hd.t < 0 || hd.t > (int64_t)0xFFFFFFFFll) return fail(ISING_EINVAL, "checkpoint sweep counter out of range");
+    unsigned long long t = (unsigned long long)hd.t;
+    if (h->n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(h->st.spins, p, h->layout.spin_bytes, cudaMemcpyHostToDevice, h->stream), "load spins");
+        p += h->layout.spin_bytes;
+        CUDA_TRY(cudaMemcpyAsync(h->st.obs, p, (size_t)h->n * 2 * sizeof(long long), cudaMemcpyHostToDevice, h->stream),
+                 "load observables");
+        p += (size_t)h->n * 2 * sizeof(long long);
+        CUDA_TRY(cudaMemcpyAsync(h->st.mom, p, (size_t)h->n * 6 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+                 "load moments");
+    }
+    CUDA_TRY(cudaMemcpyAsync(&h->st.ctl->t, &t, sizeof(t), cudaMemcpyHostToDevice, h->stream), "load counter");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    h->t = hd.t;
+    return ISING_OK;
+}
+
+int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item, int sweeps_per_unit,
+                   int threads) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (plan != ISING_PLAN_AUTO && plan != ISING_PLAN_RESIDENT && plan != ISING_PLAN_STREAM)
+        return fail(ISING_EINVAL, "unknown plan %d", plan);
+    if (words_per_thread != 0 && words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4)
+        return fail(ISING_EINVAL, "words_per_thread must be 0, 1, 2 or 4");
+    if (sweeps_per_unit < 0) return fail(ISING_EINVAL, "sweeps_per_unit must be >= 0");
+    if (rows_per_item < 0 || rows_per_item > 1024) return fail(ISING_EINVAL, "rows_per_item must be in [0, 1024]");
+    if (threads != 0 && (threads < 32 || threads > 1024 || threads % 32 != 0))
+        return fail(ISING_EINVAL, "threads must be 0 or a multiple of 32 in [32, 1024]");
+    Plan p = h->plan;
+    p.mode = plan;
+    p.words_per_thread = words_per_thread;
+    p.sweeps_per_unit = sweeps_per_unit;
+    p.rows_per_item = rows_per_item ? rows_per_item : 4;
+    if (plan == ISING_PLAN_STREAM) {
+        if (threads != 0 && threads > 256) return fail(ISING_EINVAL, "streaming kernel allows at most 256 threads");
+        p.stream_threads = threads ? threads : 256;
+    } else {
+        p.resident_threads = threads;
+    }
+    Plan saved = h->plan;
+    h->plan = p;
+    int rc = build_tables(h);
+    if (rc != ISING_OK) {
+        h->plan = saved;
+        build_tables(h);
+        return rc;
+    }
+    return ISING_OK;
+}
+
+int ising_set_graph(ising_t h, int on) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (on && h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");
+    h->graph = on != 0;
+    if (!h->graph) drop_graphs(h);
+    return ISING_OK;
+}
+
+void ising_destroy(ising_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    delete h;
+}
+
+}  // extern "C"

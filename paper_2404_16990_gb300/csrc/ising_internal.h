@@ -1,0 +1,86 @@
+// ising_internal.h -- device data structures shared by the host side of the
+// C ABI (ising_api.cu) and the kernels (ising_kernels.cu).  Not installed.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ising {
+
+// Per-lattice descriptor (device, read-only during sweeps).
+struct LatDesc {
+    uint64_t word_off;   // first 32-bit word of the lattice in the spin array
+    uint32_t L;          // side
+    uint32_t wn;         // 32-bit words per row and colour = L / 64
+    uint32_t sim;        // simulation index s (Philox counter word 2)
+    uint32_t key0;       // lo32(seed)
+    uint32_t key1;       // hi32(seed)
+    uint32_t thr0;       // threshold for dE = 4
+    uint32_t thr1;       // threshold for dE = 8
+    uint32_t pad;
+};
+
+// A group of equal-size lattices that one CTA keeps in shared memory.
+struct GroupDesc {
+    uint32_t member_off; // first entry of the group in the member list
+    uint32_t count;      // lattices in the group
+    uint32_t L;
+    uint32_t wn;
+};
+
+// A lattice handled by the streaming kernels, with the prefix of work items.
+struct StreamLat {
+    uint32_t lat;        // lattice index
+    uint32_t strips;     // ceil(L / rows_per_item)
+    uint32_t groups;     // wn / words_per_thread
+    uint32_t pad;
+    uint64_t item_begin; // first work item of this lattice
+};
+
+// Small device-side control block (first bytes of the workspace scratch).
+struct Control {
+    unsigned long long t;        // sweep index of the next sweep
+    unsigned int ticket;         // resident kernel: next work ticket
+    unsigned int blocks_done;    // stream kernel: blocks finished (last-block pattern)
+    int error;                   // nonzero: a bounded wait ran out (code in low bits)
+    int measure;                 // accumulate moments if nonzero
+    long long trace_cap;         // trace entries per lattice (0 = none)
+    unsigned int pad[8];
+};
+
+// Device pointers of one handle, passed by value to kernels.
+struct DevState {
+    const LatDesc* lat;
+    uint32_t* spins;
+    long long* obs;              // [n][2]  current E, M
+    long long* trace;            // [n][cap][2]
+    double* mom;                 // [n][6]  count, sum|m|, sum m^2, sum m^4, sum e, sum e^2
+    unsigned long long* acc;     // [n][2]  streaming partial sums (aligned-count, popcount)
+    Control* ctl;
+    unsigned int* done;          // resident: chunks done per group
+    const GroupDesc* groups;
+    const uint32_t* members;
+    const StreamLat* slats;
+    int n;
+};
+
+// Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
+cudaError_t launch_init_random(const DevState& st, int n_lat, cudaStream_t stream);
+cudaError_t launch_observables(const DevState& st, int n_lat, const uint32_t* lat_list,
+                               int n_list, cudaStream_t stream);
+cudaError_t launch_resident(const DevState& st, int n_groups, int64_t n_sweeps,
+                            int sweeps_per_unit, int threads, int grid, size_t smem_bytes,
+                            cudaStream_t stream);
+cudaError_t launch_stream_sweeps(const DevState& st, int n_slats, uint64_t total_items,
+                                 int words_per_thread, int rows_per_item, int threads,
+                                 int grid, int64_t n_sweeps, cudaStream_t stream);
+cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream);
+
+int resident_occupancy(int threads, size_t smem_bytes);
+int stream_occupancy(int words_per_thread, int threads);
+int device_sm_count();
+size_t device_max_smem_optin();
+cudaError_t configure_kernels();
+
+}  // namespace ising

@@ -1,0 +1,353 @@
+"""ctypes binding of libising (include/ising.h): the same names, argument
+marshalling only.  Every step of the simulation runs in the CUDA library; this
+module converts numpy/torch arguments to pointers and error codes to
+exceptions.  There is no CPU fallback: if libising.so cannot be built or
+loaded, every call raises.
+
+``IsingSim`` is a small convenience owner: it allocates the device workspace
+as a torch uint8 tensor on the current CUDA device and keeps it alive with the
+handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+ISING_OK = 0
+ISING_EINVAL = -1
+ISING_ENOMEM = -2
+ISING_ECUDA = -3
+ISING_ETIMEOUT = -4
+ISING_ESTATE = -5
+ISING_INIT_RANDOM = 0
+ISING_INIT_COLD = 1
+ISING_PLAN_AUTO = 0
+ISING_PLAN_RESIDENT = 1
+ISING_PLAN_STREAM = 2
+ISING_MIN_L = 64
+ISING_MAX_L = 65536
+
+_lock = threading.Lock()
+_lib = None
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ising error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()  # no-op when up to date; raises if nvcc fails
+        lib = ctypes.CDLL(path)
+        vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "ising_last_error": ([], ctypes.c_char_p),
+            "ising_version": ([], ctypes.c_char_p),
+            "ising_workspace_bytes": ([ctypes.c_int, ctypes.c_int, i64, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_batch_workspace_bytes": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64,
+                                             ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_uint64, ctypes.c_int, i64, vp, sz, vp], ctypes.c_int),
+            "ising_create_batch": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.c_int, i64, vp, sz, vp], ctypes.c_int),
+            "ising_sweep": ([vp, i64], ctypes.c_int),
+            "ising_sweeps_done": ([vp], i64),
+            "ising_kernel_launches": ([vp], i64),
+            "ising_observables": ([vp, i64p, i64p], ctypes.c_int),
+            "ising_trace": ([vp, i64p, i64p, i64, i64p], ctypes.c_int),
+            "ising_get_spins": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)], ctypes.c_int),
+            "ising_set_spins": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)], ctypes.c_int),
+            "ising_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+            "ising_lattice_words": ([vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_lattice_size": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising_num_sims": ([vp], ctypes.c_int),
+            "ising_set_measure": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising_reset_moments": ([vp], ctypes.c_int),
+            "ising_moments": ([vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "ising_state_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_save": ([vp, vp, sz], ctypes.c_int),
+            "ising_load": ([vp, vp, sz], ctypes.c_int),
+            "ising_set_plan": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+                               ctypes.c_int),
+            "ising_set_graph": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising_destroy": ([vp], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def ising_last_error() -> str:
+    return _load().ising_last_error().decode()
+
+
+def ising_version() -> str:
+    return _load().ising_version().decode()
+
+
+def _check(rc: int):
+    if rc != ISING_OK:
+        raise IsingError(rc, ising_last_error())
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def ising_workspace_bytes(L: int, n_sims: int, trace_cap: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(_load().ising_workspace_bytes(L, n_sims, trace_cap, ctypes.byref(out)))
+    return out.value
+
+
+def ising_batch_workspace_bytes(Ls: Sequence[int], trace_cap: int = 0) -> int:
+    La = np.ascontiguousarray(Ls, dtype=np.int32)
+    out = ctypes.c_size_t(0)
+    _check(_load().ising_batch_workspace_bytes(len(La), _ptr(La, ctypes.c_int), trace_cap, ctypes.byref(out)))
+    return out.value
+
+
+def ising_create(L: int, n_sims: int, temps: Sequence[float], seed: int, init: int, trace_cap: int,
+                 dev_workspace: int, ws_bytes: int, cuda_stream: int = 0) -> ctypes.c_void_p:
+    T = np.ascontiguousarray(temps, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(_load().ising_create(ctypes.byref(h), L, n_sims, _ptr(T, ctypes.c_double), seed, init, trace_cap,
+                                dev_workspace, ws_bytes, cuda_stream))
+    return h
+
+
+def ising_create_batch(Ls: Sequence[int], temps: Sequence[float], seeds: Sequence[int], init: int,
+                       trace_cap: int, dev_workspace: int, ws_bytes: int,
+                       cuda_stream: int = 0) -> ctypes.c_void_p:
+    La = np.ascontiguousarray(Ls, dtype=np.int32)
+    T = np.ascontiguousarray(temps, dtype=np.float64)
+    S = np.ascontiguousarray([int(s) for s in seeds], dtype=np.uint64)
+    h = ctypes.c_void_p()
+    _check(_load().ising_create_batch(ctypes.byref(h), len(La), _ptr(La, ctypes.c_int), _ptr(T, ctypes.c_double),
+                                      _ptr(S, ctypes.c_uint64), init, trace_cap, dev_workspace, ws_bytes,
+                                      cuda_stream))
+    return h
+
+
+def ising_sweep(h, n: int) -> None:
+    _check(_load().ising_sweep(h, n))
+
+
+def ising_sweeps_done(h) -> int:
+    return int(_load().ising_sweeps_done(h))
+
+
+def ising_kernel_launches(h) -> int:
+    return int(_load().ising_kernel_launches(h))
+
+
+def ising_load_from(h, host_ptr: int, nbytes: int) -> None:
+    """ising_load from a raw host address (e.g. a pinned torch tensor)."""
+    _check(_load().ising_load(h, host_ptr, nbytes))
+
+
+def ising_save_to(h, host_ptr: int, nbytes: int) -> None:
+    _check(_load().ising_save(h, host_ptr, nbytes))
+
+
+def ising_num_sims(h) -> int:
+    return int(_load().ising_num_sims(h))
+
+
+def ising_lattice_size(h, sim: int) -> int:
+    return int(_load().ising_lattice_size(h, sim))
+
+
+def ising_observables(h):
+    n = ising_num_sims(h)
+    E = np.zeros(n, dtype=np.int64)
+    M = np.zeros(n, dtype=np.int64)
+    _check(_load().ising_observables(h, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64)))
+    return E, M
+
+
+def ising_trace(h, max_sweeps: int):
+    n = ising_num_sims(h)
+    cap = max(0, int(max_sweeps))
+    E = np.zeros(max(1, n * cap), dtype=np.int64)
+    M = np.zeros(max(1, n * cap), dtype=np.int64)
+    k = ctypes.c_int64(0)
+    _check(_load().ising_trace(h, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), cap, ctypes.byref(k)))
+    k = k.value
+    return E[: n * k].reshape(n, k), M[: n * k].reshape(n, k)
+
+
+def ising_get_spins(h, sim: int) -> np.ndarray:
+    L = ising_lattice_size(h, sim)
+    if L <= 0:
+        raise IsingError(ISING_EINVAL, f"sim {sim} out of range")
+    out = np.empty((L, L), dtype=np.int8)
+    _check(_load().ising_get_spins(h, sim, _ptr(out, ctypes.c_int8)))
+    return out
+
+
+def ising_set_spins(h, sim: int, spins: np.ndarray) -> None:
+    a = np.ascontiguousarray(spins, dtype=np.int8)
+    L = ising_lattice_size(h, sim)
+    if a.shape != (L, L):
+        raise IsingError(ISING_EINVAL, f"spins must have shape ({L}, {L})")
+    _check(_load().ising_set_spins(h, sim, _ptr(a, ctypes.c_int8)))
+
+
+def ising_lattice_words(h, sim: int):
+    """(device address, number of 32-bit words) of lattice sim's packed spins."""
+    p = ctypes.c_void_p()
+    n = ctypes.c_size_t(0)
+    _check(_load().ising_lattice_words(h, sim, ctypes.byref(p), ctypes.byref(n)))
+    return int(p.value or 0), n.value
+
+
+def ising_get_thresholds(h) -> np.ndarray:
+    n = ising_num_sims(h)
+    out = np.zeros(max(1, 2 * n), dtype=np.uint32)
+    _check(_load().ising_get_thresholds(h, _ptr(out, ctypes.c_uint32)))
+    return out[: 2 * n].reshape(n, 2)
+
+
+def ising_set_measure(h, on: bool) -> None:
+    _check(_load().ising_set_measure(h, 1 if on else 0))
+
+
+def ising_reset_moments(h) -> None:
+    _check(_load().ising_reset_moments(h))
+
+
+def ising_moments(h) -> np.ndarray:
+    n = ising_num_sims(h)
+    out = np.zeros(max(1, 6 * n), dtype=np.float64)
+    _check(_load().ising_moments(h, _ptr(out, ctypes.c_double)))
+    return out[: 6 * n].reshape(n, 6)
+
+
+def ising_state_bytes(h) -> int:
+    out = ctypes.c_size_t(0)
+    _check(_load().ising_state_bytes(h, ctypes.byref(out)))
+    return out.value
+
+
+def ising_save(h) -> bytes:
+    n = ising_state_bytes(h)
+    buf = ctypes.create_string_buffer(n)
+    _check(_load().ising_save(h, ctypes.cast(buf, ctypes.c_void_p), n))
+    return buf.raw
+
+
+def ising_load(h, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(_load().ising_load(h, ctypes.cast(buf, ctypes.c_void_p), len(state)))
+
+
+def ising_set_plan(h, plan: int, words_per_thread: int = 0, rows_per_item: int = 0, sweeps_per_unit: int = 0,
+                   threads: int = 0) -> None:
+    _check(_load().ising_set_plan(h, plan, words_per_thread, rows_per_item, sweeps_per_unit, threads))
+
+
+def ising_set_graph(h, on: bool) -> None:
+    _check(_load().ising_set_graph(h, 1 if on else 0))
+
+
+def ising_destroy(h) -> None:
+    if h:
+        _load().ising_destroy(h)
+
+
+class IsingSim:
+    """Owner of one handle and its torch-allocated device workspace.
+
+    IsingSim(L=64, temps=[2.269185], seed=1) -> one or more L x L lattices with
+    one seed; IsingSim(Ls=[...], temps=[...], seeds=[...]) -> a batch of uneven
+    lattices.  `stream` is a torch.cuda.Stream (default: the current stream)."""
+
+    def __init__(self, L: Optional[int] = None, temps: Sequence[float] = (), seed: int = 0, *,
+                 Ls: Optional[Sequence[int]] = None, seeds: Optional[Sequence[int]] = None,
+                 cold: bool = False, trace_cap: int = 0, stream=None, device=None):
+        import torch
+        self._torch = torch
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        init = ISING_INIT_COLD if cold else ISING_INIT_RANDOM
+        temps = list(temps)
+        with torch.cuda.device(device):
+            if Ls is None:
+                nbytes = ising_workspace_bytes(L, len(temps), trace_cap)
+            else:
+                nbytes = ising_batch_workspace_bytes(Ls, trace_cap)
+            self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+            ptr = self.workspace.data_ptr()
+            s = self.stream.cuda_stream
+            if Ls is None:
+                self.h = ising_create(L, len(temps), temps, seed, init, trace_cap, ptr, nbytes, s)
+            else:
+                self.h = ising_create_batch(Ls, temps, seeds, init, trace_cap, ptr, nbytes, s)
+        self.n = ising_num_sims(self.h)
+
+    def sweep(self, n: int) -> None:
+        ising_sweep(self.h, n)
+
+    def observables(self):
+        return ising_observables(self.h)
+
+    def trace(self, max_sweeps: int):
+        return ising_trace(self.h, max_sweeps)
+
+    def spins(self, sim: int = 0) -> np.ndarray:
+        return ising_get_spins(self.h, sim)
+
+    def set_spins(self, sim: int, spins: np.ndarray) -> None:
+        ising_set_spins(self.h, sim, spins)
+
+    def words(self, sim: int = 0):
+        """Packed spins of lattice sim as a torch int32 view of the workspace."""
+        ptr, n = ising_lattice_words(self.h, sim)
+        off = ptr - self.workspace.data_ptr()
+        return self.workspace[off: off + 4 * n].view(self._torch.int32)
+
+    def thresholds(self) -> np.ndarray:
+        return ising_get_thresholds(self.h)
+
+    def set_plan(self, plan: int, **kw) -> None:
+        ising_set_plan(self.h, plan, **kw)
+
+    def set_graph(self, on: bool) -> None:
+        ising_set_graph(self.h, on)
+
+    @property
+    def sweeps_done(self) -> int:
+        return ising_sweeps_done(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            ising_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

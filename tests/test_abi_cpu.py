@@ -1,0 +1,113 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function include/*.h declares; workspace sizes follow the documented layout;
+invalid arguments are rejected with ISING_EINVAL before any device work."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2404_16990_gb300 import ising
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\([^;{)]*\)\s*;", text):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("ising_create", "ising_sweep", "ising_observables", "ising_create_batch",
+                     "ising_workspace_bytes", "ising_destroy", "ising_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = ising._build.build()
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert set(_declared_functions()) <= exported
+
+
+def test_library_has_no_oracle_dependency():
+    # the product library links nothing from oracle/
+    lib_path = ising._build.build()
+    out = subprocess.run(["nm", "-D", lib_path], capture_output=True, text=True).stdout
+    assert "oracle_" not in out
+    for src in glob.glob(os.path.join(ROOT, "paper_2404_16990_gb300", "**", "*.*"), recursive=True):
+        if src.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
+            text = open(src).read()
+            assert "import oracle" not in text and "from oracle" not in text, src
+
+
+def test_version_string():
+    assert "sm_103a" in ising.ising_version()
+
+
+def test_workspace_bytes_layout():
+    b1 = ising.ising_workspace_bytes(64, 1, 0)
+    b2 = ising.ising_workspace_bytes(64, 2, 0)
+    assert b2 - b1 >= 64 * 64 // 8
+    big = ising.ising_workspace_bytes(16384, 1, 1000)
+    assert big >= 16384 * 16384 // 8 + 1000 * 2 * 8
+    assert ising.ising_workspace_bytes(65536, 1, 0) >= 65536 * 65536 // 8
+    assert ising.ising_batch_workspace_bytes([64, 128], 0) >= (64 * 64 + 128 * 128) // 8
+    assert ising.ising_batch_workspace_bytes([], 0) > 0   # control block only
+    assert ising.ising_workspace_bytes(64, 0, 0) == ising.ising_batch_workspace_bytes([], 0)
+
+
+@pytest.mark.parametrize("L", [0, 2, 32, 63, 96, 100, 65600, -64])
+def test_invalid_sizes_rejected(L):
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_workspace_bytes(L, 1, 0)
+    assert e.value.code == ising.ISING_EINVAL
+    assert "L=" in ising.ising_last_error()
+
+
+def test_invalid_create_arguments_rejected_before_device_work():
+    fake = 1 << 40  # never dereferenced: validation fails first
+    for L, temps in [(64, [0.0]), (64, [-1.0]), (64, [float("nan")]), (64, [float("inf")]), (60, [2.0])]:
+        with pytest.raises(ising.IsingError) as e:
+            ising.ising_create(L, 1, temps, 1, 0, 0, fake, 1 << 30, 0)
+        assert e.value.code == ising.ISING_EINVAL
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_create(64, 1, [2.0], 1, 7, 0, fake, 1 << 30, 0)       # bad init mode
+    assert e.value.code == ising.ISING_EINVAL
+    need = ising.ising_workspace_bytes(64, 1, 0)
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_create(64, 1, [2.0], 1, 0, 0, fake, need - 1, 0)      # workspace too small
+    assert e.value.code == ising.ISING_ENOMEM
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_create(64, 1, [2.0], 1, 0, 0, fake + 8, need, 0)      # misaligned
+    assert e.value.code == ising.ISING_EINVAL
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_create(64, 1, [2.0], 1, 0, -1, fake, need, 0)         # negative trace
+    assert e.value.code == ising.ISING_EINVAL
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_create_batch([64, 96], [2.0, 2.0], [1, 2], 0, 0, fake, 1 << 30, 0)
+    assert e.value.code == ising.ISING_EINVAL
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = ising._load()
+    assert lib.ising_sweep(None, 1) == ising.ISING_EINVAL
+    assert lib.ising_sweeps_done(None) == -1
+    assert lib.ising_num_sims(None) == 0
+    lib.ising_destroy(None)
