@@ -162,6 +162,20 @@ int ising_reset_moments(ising_t h);
  * m = M/L^2 and e = E/L^2.  Synchronises. */
 int ising_moments(ising_t h, double* out);
 
+/* Binder cumulant U = 1 - <m^4> / (3 <m^2>^2) of every lattice from the
+ * moment sums of ising_moments (moments[6*i + 0..5]); U[i] is NaN where no
+ * sweep was measured.  Host-only. */
+int ising_binder(const double* moments, int n_sims, double* U);
+
+/* Integrated autocorrelation time of the series x[0..n-1] (n >= 2), host-only:
+ * tau = 1/2 + sum_{t=1..W} rho(t) with rho the normalised autocovariance and W
+ * the smallest lag with W >= c * tau(W) (automatic window of Madras and Sokal,
+ * c ~ 5..6).  tau_err (may be NULL) = tau * sqrt(2(2W+1)/n), window (may be
+ * NULL) = W.  A constant series gives tau = 1/2.  The paper averages |M| over
+ * long runs (Section 3.1); effective independent samples = n / (2 tau). */
+int ising_tau_int(const double* x, int64_t n, double c, double* tau, double* tau_err,
+                  int64_t* window);
+
 /* Size of a checkpoint of the handle (spins, sweep counter, current E/M,
  * moment sums), and save/load through a host buffer of that size.  Loading
  * into a handle of a different shape is ISING_EINVAL.  Because the generator

@@ -108,6 +108,8 @@ struct Plan {
 
 }  // namespace
 
+int ising::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct ising_handle {
     int n = 0;
     std::vector<int> L;

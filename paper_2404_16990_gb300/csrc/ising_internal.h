@@ -77,6 +77,9 @@ cudaError_t launch_stream_sweeps(const DevState& st, int n_slats, uint64_t total
                                  int grid, int64_t n_sweeps, cudaStream_t stream);
 cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream);
 
+// Record a message for ising_last_error() and return code (ising_api.cu).
+int set_last_error(int code, const char* msg);
+
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);
 int device_sm_count();

@@ -88,6 +88,10 @@ def _load():
                                ctypes.c_int),
             "ising_set_graph": ([vp, ctypes.c_int], ctypes.c_int),
             "ising_destroy": ([vp], None),
+            "ising_binder": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+                             ctypes.c_int),
+            "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), i64p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -274,6 +278,22 @@ def ising_set_graph(h, on: bool) -> None:
 def ising_destroy(h) -> None:
     if h:
         _load().ising_destroy(h)
+
+
+def ising_binder(moments: np.ndarray) -> np.ndarray:
+    m = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1, 6)
+    U = np.zeros(max(1, len(m)), dtype=np.float64)
+    _check(_load().ising_binder(_ptr(m, ctypes.c_double), len(m), _ptr(U, ctypes.c_double)))
+    return U[: len(m)]
+
+
+def ising_tau_int(x, c: float = 6.0):
+    """(tau_int, error, window) of a 1-D series (Madras-Sokal automatic window)."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    tau, err, w = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
+    _check(_load().ising_tau_int(_ptr(a, ctypes.c_double), len(a), c, ctypes.byref(tau), ctypes.byref(err),
+                                 ctypes.byref(w)))
+    return tau.value, err.value, w.value
 
 
 class IsingSim:
