@@ -206,6 +206,43 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
  * captured for that n (1 = on, 0 = off).  Results are identical either way. */
 int ising_set_graph(ising_t h, int on);
 
+/* Allocation-free streaming sweep.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * inside a host application that owns all device memory through its own pool,
+ * or a latency-critical path where cudaMalloc may block or synchronise the
+ * device -- and so cannot provide the workspace the other calls need.
+ *
+ * It runs the same streaming half-sweep kernel as ising_sweep, with the
+ * kernel's scratch (lattice descriptors, per-lattice partial sums of E and M,
+ * the sweep counter and block counter) in one fixed device array inside the
+ * library of about 5.4 KB, sized for at most ISING_NOALLOC_MAX_LATTICES
+ * lattices; a larger n_lat is ISING_EINVAL.  Every GPU that loads the library
+ * holds that array until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ *
+ *   dev_words  device, 16-byte aligned: the packed lattices one after another,
+ *              lattice i (side Ls[i]) taking Ls[i]^2/32 32-bit words in the
+ *              layout described at the top of this file; updated in place.
+ *   Ls, temps, seeds  host arrays [n_lat]; lattice i uses key seeds[i] and
+ *              simulation index s = i (as ising_create_batch).
+ *   t0, n      sweeps t0 .. t0+n-1 (t0 is the Philox sweep counter of the
+ *              first sweep; t0 + n < 2^32).  n = 0 does nothing.
+ *   dev_EM     device int64[2*n_lat]: E and M of lattice i after the last
+ *              sweep at [2i] and [2i+1].
+ *
+ * Asynchronous on cuda_stream.  All calls share the one scratch array, which
+ * keeps the last call's contents; each call clears what must start at zero.
+ * Calls that overlap on the GPU (other streams, or other host threads without
+ * ordering between them) race on the array and give undefined results.  The
+ * first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Results are bit-identical to ising_create_batch
+ * followed by ising_sweep on the same lattices when ising_sweeps_done == t0. */
+#define ISING_NOALLOC_MAX_LATTICES 64
+int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls, const double* temps,
+                        const uint64_t* seeds, int64_t t0, int64_t n, int64_t* dev_EM,
+                        void* cuda_stream);
+
 /* Free the handle (not the workspace).  Synchronises its stream. */
 void ising_destroy(ising_t h);
 

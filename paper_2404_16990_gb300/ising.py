@@ -88,6 +88,8 @@ def _load():
                                ctypes.c_int),
             "ising_set_graph": ([vp, ctypes.c_int], ctypes.c_int),
             "ising_destroy": ([vp], None),
+            "ising_sweep_noalloc": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_uint64), i64, i64, vp, vp], ctypes.c_int),
             "ising_binder": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -278,6 +280,20 @@ def ising_set_graph(h, on: bool) -> None:
 def ising_destroy(h) -> None:
     if h:
         _load().ising_destroy(h)
+
+
+ISING_NOALLOC_MAX_LATTICES = 64
+
+
+def ising_sweep_noalloc(dev_words: int, Ls: Sequence[int], temps: Sequence[float], seeds: Sequence[int],
+                        t0: int, n: int, dev_EM: int, cuda_stream: int = 0) -> None:
+    """Allocation-free sweep of packed lattices held by the caller (device
+    addresses dev_words and dev_EM); see ising_sweep_noalloc in ising.h."""
+    La = np.ascontiguousarray(Ls, dtype=np.int32)
+    T = np.ascontiguousarray(temps, dtype=np.float64)
+    S = np.ascontiguousarray([int(s) for s in seeds], dtype=np.uint64)
+    _check(_load().ising_sweep_noalloc(dev_words, len(La), _ptr(La, ctypes.c_int), _ptr(T, ctypes.c_double),
+                                       _ptr(S, ctypes.c_uint64), t0, n, dev_EM, cuda_stream))
 
 
 def ising_binder(moments: np.ndarray) -> np.ndarray:
