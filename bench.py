@@ -40,8 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["l16384", "batch754"], default="l16384")
     ap.add_argument("--L", type=int, default=16384)
-    ap.add_argument("--sweeps", type=int, default=1000)
+    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754)")
+    ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -127,7 +129,7 @@ def time_oracle(L: int, seconds: float, max_sweeps: int | None = None):
     lat = oracle.init(L, 2, 0, n_threads=cores)
     done, t_total = 0, 0.0
     n = 1
-    while t_total < seconds and (max_sweeps is None or done < max_sweeps):
+    while (t_total < seconds or done == 0) and (max_sweeps is None or done < max_sweeps):
         if max_sweeps is not None:
             n = min(n, max_sweeps - done)
         t0 = time.perf_counter()
@@ -183,17 +185,30 @@ def ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    L, n_sw = args.L, args.sweeps
-    seed = 2 + 1000 * rank  # independent replicas per rank; rank 0 is the configured seed 2
+    L = args.L
     sims = []
-    with torch.cuda.stream(stream):
-        for cold in (True, False):
-            s = ising.IsingSim(Ls=[L] * 3, temps=list(T_RUNS), seeds=[seed] * 3, cold=cold,
-                               trace_cap=n_sw, stream=stream, device=dev)
-            s.set_graph(True)
+    tuned = None
+    if args.workload == "l16384":
+        n_sw = args.sweeps or 1000
+        seed = 2 + 1000 * rank  # independent replicas per rank; rank 0 is the configured seed 2
+        with torch.cuda.stream(stream):
+            for cold in (True, False):
+                s = ising.IsingSim(Ls=[L] * 3, temps=list(T_RUNS), seeds=[seed] * 3, cold=cold,
+                                   trace_cap=n_sw, stream=stream, device=dev)
+                sims.append(s)
+    else:
+        from paper_2404_16990_gb300 import workloads
+        n_sw = args.sweeps or 10000
+        wl = workloads.batch754(master_seed=20240426 + rank)
+        with torch.cuda.stream(stream):
+            s = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=0, stream=stream, device=dev)
             sims.append(s)
+    if args.autotune or args.workload == "batch754":
+        tuned = [s.autotune(probe_sweeps=20 if args.workload == "batch754" else 5) for s in sims]
+    for s in sims:
+        s.set_graph(True)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    sites = sum(sum(L * L for _ in range(3)) for _ in sims)
+    sites = sum(sum(int(ising.ising_lattice_size(s.h, i)) ** 2 for i in range(s.n)) for s in sims)
     flips_per_step = sites * n_sw
 
     def step():
@@ -234,10 +249,21 @@ def ours(args):
     ms_per_step = total_ms / args.steps
     value = flips_per_step * ws / (ms_per_step * 1e6)
 
-    # dominant kernel: streaming half-sweep, 2 launches per sweep per handle
-    n_half = 2 * n_sw * len(sims) * args.steps
-    avg_launch_s = (sum(step_ms) / 1e3) / n_half
-    sites_per_launch = sites // 2 // len(sims)     # half the sites of one handle's three lattices
+    # dominant kernel: for the 16384^2 workload the streaming half-sweep (2
+    # launches per sweep per handle); for the batch the persistent resident
+    # kernel (one launch per step); either way the algorithmic ops of the
+    # timed region over its duration
+    plan = ising.ising_get_plan(sims[0].h)
+    if args.workload == "l16384":
+        n_launch = 2 * n_sw * len(sims) * args.steps
+        kname = "stream_half_kernel"
+    else:
+        n_launch = args.steps
+        kname = "resident_kernel" if plan["plan"] != ising.ISING_PLAN_STREAM else "stream_half_kernel"
+        if kname == "stream_half_kernel":
+            n_launch = 2 * n_sw * args.steps
+    avg_launch_s = (sum(step_ms) / 1e3) / n_launch
+    sites_per_launch = flips_per_step * args.steps / n_launch
     achieved = OPS_PER_SITE * sites_per_launch / avg_launch_s / 1e12
     peak = SMS * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -272,25 +298,34 @@ def ours(args):
                "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "l16384":
         cpu = time_oracle(L, args.cpu_seconds)
         cpu.pop("seconds", None)
 
     if rank == 0:
+        if args.workload == "l16384":
+            cfg = {"workload": f"six {L}x{L} periodic lattices, T in {{1.5, 2.269185, 3.0}} x "
+                               f"{{cold, random seed 2}}, {n_sw} checkerboard sweeps per step, "
+                               f"E/M recorded every sweep",
+                   "lattices_per_gpu": 6, "L": L, "sweeps_per_step": n_sw,
+                   "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps; "
+                   "working set 192 MiB > 129 MB L2", "kernel": "streaming half-sweep, CUDA graph",
+                   "plan": plan}
+        else:
+            cfg = {"workload": f"754 lattices, L in {{128,256,512,1024}} log-uniform, T ~ U[1.8,2.8], "
+                               f"random starts, {n_sw} sweeps per step, one persistent launch per step",
+                   "lattices_per_gpu": 754, "spins_per_gpu": sites, "sweeps_per_step": n_sw,
+                   "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps",
+                   "kernel": kname + ", CUDA graph", "plan": plan, "autotune_probe_flip_per_ns": tuned}
         line = {
             "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"six {L}x{L} periodic lattices, T in {{1.5, 2.269185, 3.0}} x "
-                                   f"{{cold, random seed 2}}, {n_sw} checkerboard sweeps per step, "
-                                   f"E/M recorded every sweep",
-                       "lattices_per_gpu": 6, "L": L, "sweeps_per_step": n_sw,
-                       "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps; "
-                       "working set 192 MiB > 129 MB L2", "kernel": "streaming half-sweep, CUDA graph"},
+            "config": cfg,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "stream_half_kernel", "ops_per_site": OPS_PER_SITE,
+                         "kernel": kname, "ops_per_site": OPS_PER_SITE,
                          "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": cpu,
             "e2e": e2e,

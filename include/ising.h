@@ -202,6 +202,22 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
 int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int sweeps_per_unit, int threads);
 
+/* Autotuner: time candidate plans (resident with sweeps_per_unit in {8, 32,
+ * 128} and block sizes {auto, 512, 1024} when some lattice has L <= 1024;
+ * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {2, 4, 8},
+ * threads in {128, 256}) for probe_sweeps sweeps each on the handle's stream
+ * and keep the fastest.  The lattices and the sweep counter are saved before
+ * and restored after, so tuning changes no result.  If the environment
+ * variable ISING_TUNE_CACHE names a file, the choice is appended to it keyed by
+ * the multiset of lattice sizes and the device, and a later call with
+ * force = 0 reuses it without timing.  *best_flips_per_ns (may be NULL)
+ * receives the winner's probe rate (0 when taken from the cache). */
+int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flips_per_ns);
+
+/* The plan in use (any pointer may be NULL). */
+int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_item,
+                   int* sweeps_per_unit, int* threads);
+
 /* Replay the sweeps of each later ising_sweep(h, n) call through a CUDA graph
  * captured for that n (1 = on, 0 = off).  Results are identical either way. */
 int ising_set_graph(ising_t h, int on);

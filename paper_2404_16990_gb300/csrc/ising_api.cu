@@ -747,6 +747,146 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
     return ISING_OK;
 }
 
+namespace {
+
+struct TuneCand {
+    int mode, V, R, k, threads;
+};
+
+std::string tune_key(const ising_handle* h) {
+    std::vector<int> Ls = h->L;
+    std::sort(Ls.begin(), Ls.end());
+    std::string key;
+    int run = 0;
+    for (size_t i = 0; i < Ls.size(); ++i) {
+        ++run;
+        if (i + 1 == Ls.size() || Ls[i + 1] != Ls[i]) {
+            key += std::to_string(Ls[i]) + "x" + std::to_string(run) + ",";
+            run = 0;
+        }
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    key += "sm" + std::to_string(prop.major * 10 + prop.minor) + "n" + std::to_string(prop.multiProcessorCount);
+    return key;
+}
+
+bool tune_cache_lookup(const std::string& key, TuneCand* c) {
+    const char* path = getenv("ISING_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char kbuf[4096];
+    TuneCand t{};
+    bool found = false;
+    while (fscanf(f, "%4095s %d %d %d %d %d", kbuf, &t.mode, &t.V, &t.R, &t.k, &t.threads) == 6)
+        if (key == kbuf) { *c = t; found = true; }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string& key, const TuneCand& c) {
+    const char* path = getenv("ISING_TUNE_CACHE");
+    if (!path || !*path || key.size() >= 4000) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.mode, c.V, c.R, c.k, c.threads);
+    fclose(f);
+}
+
+int apply_cand(ising_handle* h, const TuneCand& c) {
+    return ising_set_plan(h, c.mode, c.V, c.R, c.k, c.threads);
+}
+
+}  // namespace
+
+int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flips_per_ns) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (probe_sweeps < 1) return fail(ISING_EINVAL, "probe_sweeps must be >= 1");
+    if (best_flips_per_ns) *best_flips_per_ns = 0.0;
+    if (h->n == 0) return ISING_OK;
+    const std::string key = tune_key(h);
+    TuneCand cached{};
+    if (!force && tune_cache_lookup(key, &cached)) {
+        int rc = apply_cand(h, cached);
+        if (rc == ISING_OK) return ISING_OK;
+    }
+    // candidates: resident (lattices up to L = 1024) with several unit sizes
+    // and block sizes, and the streaming kernel with several tilings
+    std::vector<TuneCand> cands;
+    bool any_resident = false;
+    for (int L : h->L) any_resident |= (L <= 1024);
+    if (any_resident)
+        for (int k : {8, 32, 128})
+            for (int thr : {0, 512, 1024}) cands.push_back({ISING_PLAN_AUTO, 0, 4, k, thr});
+    const int Vs[] = {1, 2, 4};
+    for (int V : Vs) {
+        bool ok = true;
+        for (int L : h->L) ok &= ((L / 64) % V == 0);
+        if (!ok) continue;
+        for (int R : {2, 4, 8})
+            for (int thr : {128, 256}) cands.push_back({ISING_PLAN_STREAM, V, R, 0, thr});
+    }
+    size_t nbytes = 0;
+    int rc = ising_state_bytes(h, &nbytes);
+    if (rc != ISING_OK) return rc;
+    std::vector<char> saved(nbytes);
+    rc = ising_save(h, saved.data(), nbytes);
+    if (rc != ISING_OK) return rc;
+    const Plan plan0 = h->plan;
+    const bool graph0 = h->graph;
+    h->graph = false;
+    double sites = 0;
+    for (int L : h->L) sites += (double)L * L;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    double best = -1.0;
+    TuneCand best_c{};
+    for (const TuneCand& c : cands) {
+        if (apply_cand(h, c) != ISING_OK) continue;
+        if (ising_load(h, saved.data(), nbytes) != ISING_OK) break;
+        if (ising_sweep(h, 1) != ISING_OK) continue;                 // warm-up (graph-free)
+        cudaEventRecord(e0, h->stream);
+        if (ising_sweep(h, probe_sweeps) != ISING_OK) continue;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = sites * (double)probe_sweeps / ((double)ms * 1e6);
+        if (rate > best) { best = rate; best_c = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->graph = graph0;
+    if (best < 0) {
+        h->plan = plan0;
+        build_tables(h);
+        ising_load(h, saved.data(), nbytes);
+        return fail(ISING_ECUDA, "autotune: no candidate ran");
+    }
+    rc = apply_cand(h, best_c);
+    if (rc != ISING_OK) return rc;
+    rc = ising_load(h, saved.data(), nbytes);   // the state is as before tuning
+    if (rc != ISING_OK) return rc;
+    tune_cache_store(key, best_c);
+    if (best_flips_per_ns) *best_flips_per_ns = best;
+    return ISING_OK;
+}
+
+int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_item, int* sweeps_per_unit,
+                   int* threads) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (plan) *plan = h->plan.mode;
+    if (words_per_thread) *words_per_thread = h->V;
+    if (rows_per_item) *rows_per_item = h->plan.rows_per_item;
+    if (sweeps_per_unit) *sweeps_per_unit = h->plan.sweeps_per_unit;
+    if (threads) *threads = h->plan.mode == ISING_PLAN_STREAM ? h->plan.stream_threads : h->res_threads;
+    return ISING_OK;
+}
+
 int ising_set_graph(ising_t h, int on) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (on && h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");

@@ -88,15 +88,21 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t w, uint32_t up, uin
     const uint32_t need8 = b2;
     const uint32_t need4 = b0 & b1;                 // a == 3
     uint32_t flip = ~(need4 | need8);
+    // per-site threshold: thr0 ^ (dx & -bit) picks thr1 where need8 is set,
+    // without a branch or a predicate select
+    const uint32_t dx = key.thr0 ^ key.thr1;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
         const uint4 r = philox(q0 + (uint32_t)g, key.t, key.s, key.phase, key.k0, key.k1);
         const uint32_t n8 = need8 >> (4 * g);
-        uint32_t acc = (r.x < ((n8 & 1u) ? key.thr1 : key.thr0)) ? 1u : 0u;
-        acc |= (r.y < ((n8 & 2u) ? key.thr1 : key.thr0)) ? 2u : 0u;
-        acc |= (r.z < ((n8 & 4u) ? key.thr1 : key.thr0)) ? 4u : 0u;
-        acc |= (r.w < ((n8 & 8u) ? key.thr1 : key.thr0)) ? 8u : 0u;
-        flip |= acc << (4 * g);
+        const uint32_t t0 = key.thr0 ^ (dx & (0u - (n8 & 1u)));
+        const uint32_t t1 = key.thr0 ^ (dx & (0u - ((n8 >> 1) & 1u)));
+        const uint32_t t2 = key.thr0 ^ (dx & (0u - ((n8 >> 2) & 1u)));
+        const uint32_t t3 = key.thr0 ^ (dx & (0u - ((n8 >> 3) & 1u)));
+        if (r.x < t0) flip |= 1u << (4 * g + 0);
+        if (r.y < t1) flip |= 1u << (4 * g + 1);
+        if (r.z < t2) flip |= 1u << (4 * g + 2);
+        if (r.w < t3) flip |= 1u << (4 * g + 3);
     }
     return w ^ flip;
 }
@@ -385,7 +391,7 @@ __device__ __forceinline__ void store_vec(uint32_t* p, const uint32_t (&o)[V]) {
 }
 
 template <int V>
-__global__ void __launch_bounds__(256) stream_half_kernel(DevState st, int n_slats,
+__global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_slats,
                                                           unsigned long long total_tiles,
                                                           int R, uint32_t c) {
     __shared__ unsigned long long red[64];

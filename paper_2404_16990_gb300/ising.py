@@ -87,6 +87,8 @@ def _load():
             "ising_set_plan": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
                                ctypes.c_int),
             "ising_set_graph": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising_autotune": ([vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "ising_get_plan": ([vp] + [ctypes.POINTER(ctypes.c_int)] * 5, ctypes.c_int),
             "ising_destroy": ([vp], None),
             "ising_sweep_noalloc": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_uint64), i64, i64, vp, vp], ctypes.c_int),
@@ -273,6 +275,18 @@ def ising_set_plan(h, plan: int, words_per_thread: int = 0, rows_per_item: int =
     _check(_load().ising_set_plan(h, plan, words_per_thread, rows_per_item, sweeps_per_unit, threads))
 
 
+def ising_autotune(h, probe_sweeps: int = 10, force: bool = False) -> float:
+    best = ctypes.c_double(0)
+    _check(_load().ising_autotune(h, probe_sweeps, 1 if force else 0, ctypes.byref(best)))
+    return best.value
+
+
+def ising_get_plan(h) -> dict:
+    v = [ctypes.c_int(0) for _ in range(5)]
+    _check(_load().ising_get_plan(h, *[ctypes.byref(x) for x in v]))
+    return dict(zip(["plan", "words_per_thread", "rows_per_item", "sweeps_per_unit", "threads"], [x.value for x in v]))
+
+
 def ising_set_graph(h, on: bool) -> None:
     _check(_load().ising_set_graph(h, 1 if on else 0))
 
@@ -369,6 +383,9 @@ class IsingSim:
 
     def set_plan(self, plan: int, **kw) -> None:
         ising_set_plan(self.h, plan, **kw)
+
+    def autotune(self, probe_sweeps: int = 10, force: bool = False) -> float:
+        return ising_autotune(self.h, probe_sweeps, force)
 
     def set_graph(self, on: bool) -> None:
         ising_set_graph(self.h, on)

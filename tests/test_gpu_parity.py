@@ -302,3 +302,28 @@ def test_temperature_limits_on_gpu():
     s0 = hot.spins(0)
     hot.sweep(1)
     assert np.array_equal(hot.spins(0), -s0)
+
+
+def test_autotune_keeps_state_and_bits(tmp_path, monkeypatch):
+    monkeypatch.setenv("ISING_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    wl = workloads.random_batch(12, Ls=(64, 128, 256, 1152), seed=31)
+    sim = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=6)
+    sim.sweep(3)
+    before = [sim.spins(i) for i in range(sim.n)]
+    E0, M0 = sim.observables()
+    assert sim.autotune(probe_sweeps=3, force=True) > 0
+    assert sim.sweeps_done == 3
+    for i in range(sim.n):
+        assert np.array_equal(sim.spins(i), before[i])
+    assert all(np.array_equal(a, b) for a, b in zip((E0, M0), sim.observables()))
+    sim.sweep(6)
+    refs = [oracle.init(L, s, i) for i, (L, s) in enumerate(zip(wl.Ls, wl.seeds))]
+    Eo, Mo = oracle.sweeps_batch(refs, wl.temps, wl.seeds, list(range(len(refs))), 0, 9, NT)
+    Eg, Mg = sim.trace(6)
+    assert np.array_equal(Eg, Eo[:, 3:]) and np.array_equal(Mg, Mo[:, 3:])
+    for i in range(len(refs)):
+        assert np.array_equal(sim.spins(i), refs[i])
+    plan = ising.ising_get_plan(sim.h)
+    sim2 = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds)
+    assert sim2.autotune(probe_sweeps=3, force=False) == 0.0      # taken from the cache
+    assert ising.ising_get_plan(sim2.h)["plan"] == plan["plan"]
