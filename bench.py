@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--L", type=int, default=16384)
     ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754)")
     ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
+    ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream"], default="tuned",
+                    help="batch754: force a plan instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -203,7 +205,12 @@ def ours(args):
         with torch.cuda.stream(stream):
             s = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=0, stream=stream, device=dev)
             sims.append(s)
-    if args.autotune or args.workload == "batch754":
+    if args.workload == "batch754" and args.plan != "tuned":
+        code = {"auto": ising.ISING_PLAN_AUTO, "resident": ising.ISING_PLAN_RESIDENT,
+                "stream": ising.ISING_PLAN_STREAM}[args.plan]
+        for s in sims:
+            s.set_plan(code)
+    elif args.autotune or args.workload == "batch754":
         tuned = [s.autotune(probe_sweeps=20 if args.workload == "batch754" else 5) for s in sims]
     for s in sims:
         s.set_graph(True)

@@ -233,7 +233,8 @@ int build_tables(ising_handle* h) {
         size_t max_words = 0;
         for (auto& g : groups) max_words = std::max(max_words, (size_t)g.count * g.L * g.wn);
         int thr = h->plan.resident_threads;
-        if (thr <= 0) thr = (int)std::min<size_t>(1024, std::max<size_t>(64, (max_words + 31) / 32 * 32));
+        if (thr <= 0) thr = (int)std::min<size_t>(512, std::max<size_t>(64, (max_words + 31) / 32 * 32));
+        if (thr > 512) return fail(ISING_EINVAL, "resident kernel runs at most 512 threads per block");
         h->res_threads = thr;
         const int occ = resident_occupancy(thr, h->group_smem);
         if (occ <= 0)
@@ -820,7 +821,7 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     for (int L : h->L) any_resident |= (L <= 1024);
     if (any_resident)
         for (int k : {8, 32, 128})
-            for (int thr : {0, 512, 1024}) cands.push_back({ISING_PLAN_AUTO, 0, 4, k, thr});
+            for (int thr : {0, 256, 512}) cands.push_back({ISING_PLAN_AUTO, 0, 4, k, thr});
     const int Vs[] = {1, 2, 4};
     for (int V : Vs) {
         bool ok = true;

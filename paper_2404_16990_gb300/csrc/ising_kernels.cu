@@ -248,7 +248,7 @@ __global__ void observables_finalize_kernel(DevState st, const uint32_t* list, i
 // chunk c-1 of its group is stored.  The oldest ticket in flight never waits,
 // so the schedule always progresses.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) resident_kernel(DevState st, int n_groups, long long n_sweeps,
+__global__ void __launch_bounds__(512, 1) resident_kernel(DevState st, int n_groups, long long n_sweeps,
                                                         int k_unit) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ unsigned long long s_cnt[2 * kMaxGroupCount];
@@ -308,44 +308,53 @@ __global__ void __launch_bounds__(1024) resident_kernel(DevState st, int n_group
 
         const long long sw0 = chunk * k_unit;
         const long long k_this = (n_sweeps - sw0 < k_unit) ? (n_sweeps - sw0) : k_unit;
+        // threads as a (ty, tx) grid over the group's stacked rows (lattice m
+        // holds rows [m*L, (m+1)*L)) and the words of a row: no divisions in
+        // the update loop
+        const uint32_t tw = wn < (uint32_t)nthr ? wn : (uint32_t)nthr;
+        const uint32_t n_ty = (uint32_t)nthr / tw;
+        const uint32_t tx = (uint32_t)tid % tw, ty = (uint32_t)tid / tw;
+        const uint32_t rows = cnt * L;
         for (long long it = 0; it < k_this; ++it) {
             const unsigned long long t = s_t0 + (unsigned long long)(sw0 + it);
             if (tid < 2 * (int)cnt) s_cnt[tid] = 0;
             for (uint32_t c = 0; c < 2; ++c) {
                 unsigned long long sa = 0, sp = 0;
-                uint32_t m_cur = 0xFFFFFFFFu;
-                for (uint32_t idx = tid; idx < cnt * wpc; idx += nthr) {
-                    const uint32_t m = idx / wpc, rem = idx - m * wpc;
-                    const uint32_t y = rem / wn, k = rem - y * wn;
-                    uint32_t* lat_sm = sm + (size_t)m * wpl;
-                    const uint32_t* opp = lat_sm + (1u - c) * wpc;
-                    const uint32_t ym = (y == 0) ? L - 1 : y - 1, yp = (y + 1 == L) ? 0 : y + 1;
-                    const bool plus = ((c ^ (y & 1u)) != 0);
-                    const uint32_t kk = plus ? ((k + 1 == wn) ? 0 : k + 1) : ((k == 0) ? wn - 1 : k - 1);
-                    const uint32_t up = opp[ym * wn + k], dn = opp[yp * wn + k];
-                    const uint32_t same = opp[y * wn + k];
-                    const uint32_t side = side_word(plus, same, opp[y * wn + kk]);
-                    SiteKey key = s_key[m];
-                    key.t = (uint32_t)t;
-                    key.phase = c;
-                    uint32_t* own = lat_sm + c * wpc + y * wn + k;
-                    const uint32_t q0 = (y * (L >> 1) + 32u * k) >> 2;
-                    const uint32_t wnew = metropolis_word(*own, up, dn, same, side, q0, key);
-                    *own = wnew;
-                    if (c == 1) {
-                        if (m != m_cur) {
-                            if (m_cur != 0xFFFFFFFFu) {
-                                atomicAdd(&s_cnt[2 * m_cur], sa);
-                                atomicAdd(&s_cnt[2 * m_cur + 1], sp);
+                uint32_t m = 0, row0 = 0;
+                if (ty < n_ty) {
+                    for (uint32_t Y = ty; Y < rows; Y += n_ty) {
+                        if (Y >= row0 + L) {
+                            if (c == 1) {
+                                atomicAdd(&s_cnt[2 * m], sa);
+                                atomicAdd(&s_cnt[2 * m + 1], sp);
+                                sa = 0; sp = 0;
                             }
-                            m_cur = m; sa = 0; sp = 0;
+                            do { ++m; row0 += L; } while (Y >= row0 + L);
                         }
-                        observe_word(wnew, up, dn, same, side, sa, sp);
+                        const uint32_t y = Y - row0;
+                        uint32_t* lat_sm = sm + (size_t)m * wpl;
+                        const uint32_t* opp = lat_sm + (1u - c) * wpc;
+                        const uint32_t ym = (y == 0) ? L - 1 : y - 1, yp = (y + 1 == L) ? 0 : y + 1;
+                        const bool plus = ((c ^ (y & 1u)) != 0);
+                        SiteKey key = s_key[m];
+                        key.t = (uint32_t)t;
+                        key.phase = c;
+                        for (uint32_t k = tx; k < wn; k += tw) {
+                            const uint32_t kk = plus ? ((k + 1 == wn) ? 0 : k + 1) : ((k == 0) ? wn - 1 : k - 1);
+                            const uint32_t up = opp[ym * wn + k], dn = opp[yp * wn + k];
+                            const uint32_t same = opp[y * wn + k];
+                            const uint32_t side = side_word(plus, same, opp[y * wn + kk]);
+                            uint32_t* own = lat_sm + c * wpc + y * wn + k;
+                            const uint32_t q0 = (y * (L >> 1) + 32u * k) >> 2;
+                            const uint32_t wnew = metropolis_word(*own, up, dn, same, side, q0, key);
+                            *own = wnew;
+                            if (c == 1) observe_word(wnew, up, dn, same, side, sa, sp);
+                        }
                     }
-                }
-                if (c == 1 && m_cur != 0xFFFFFFFFu) {
-                    atomicAdd(&s_cnt[2 * m_cur], sa);
-                    atomicAdd(&s_cnt[2 * m_cur + 1], sp);
+                    if (c == 1) {
+                        atomicAdd(&s_cnt[2 * m], sa);
+                        atomicAdd(&s_cnt[2 * m + 1], sp);
+                    }
                 }
                 __syncthreads();
             }

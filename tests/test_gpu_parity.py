@@ -92,7 +92,7 @@ def test_streaming_kernel_bit_exact(L, V, R, T, cold):
     assert np.array_equal(sim.spins(0), ref)
 
 
-@pytest.mark.parametrize("L,k,threads", [(64, 1, 64), (192, 3, 96), (256, 8, 0), (512, 5, 1024), (1024, 2, 1024)])
+@pytest.mark.parametrize("L,k,threads", [(64, 1, 64), (192, 3, 96), (256, 8, 0), (512, 5, 512), (1024, 2, 512)])
 def test_resident_kernel_bit_exact(L, k, threads):
     n = 11
     T = [1.8, TC, 2.9][L % 3]
