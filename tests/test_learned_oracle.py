@@ -1,0 +1,152 @@
+"""Pins for the learned-proposal oracle: finite-difference gradients, the
+autoregressive mask property, normalisation of q, the local energy against
+the full Hamiltonian, exact detailed balance of the MH patch move on a 4x4
+torus (all 2^16 states), bf16 rounding against torch, and one Adam step."""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import learned as ol
+
+
+def rand_windows(B, S, seed):
+    rng = np.random.default_rng(seed)
+    return np.where(rng.random((B, S, S)) < 0.5, -1, 1).astype(np.int8)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(10000) * 10 ** rng.uniform(-5, 5, 10000),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 0.0, 65504.0]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ol.bf16(x), ref)
+
+
+def test_gradient_matches_finite_differences():
+    win = rand_windows(6, 10, 1)
+    flat = ol.init_params(3, gain=1.5)
+    g = ol.grad(win, flat, exact=True)
+    rng = np.random.default_rng(2)
+    idx = list(rng.integers(0, ol.N_PARAMS, size=40)) + [0, 16 * 16 - 1, ol.N_PARAMS - 1]
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(ol.N_PARAMS)
+        e[i] = h
+        fd = (ol.loss(win, flat + e, exact=True) - ol.loss(win, flat - e, exact=True)) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+    d = rng.standard_normal(ol.N_PARAMS)
+    fd = (ol.loss(win, flat + 1e-6 * d, exact=True) - ol.loss(win, flat - 1e-6 * d, exact=True)) / 2e-6
+    assert abs(fd - g @ d) < 1e-5 * max(1.0, abs(fd))
+
+
+def test_autoregressive_mask():
+    # z at interior position p depends only on ring values and earlier interior values
+    win = rand_windows(4, 10, 5)
+    flat = ol.init_params(7, gain=2.0)
+    z0, _ = ol.forward(win, flat, exact=True)
+    for (r, c) in [(1, 1), (3, 5), (8, 8), (5, 1)]:
+        w2 = win.copy()
+        w2[:, r, c] *= -1
+        z1, _ = ol.forward(w2, flat, exact=True)
+        order = np.arange(100).reshape(10, 10)
+        before = order <= order[r, c]
+        assert np.array_equal(z0[:, before], z1[:, before])
+        assert not np.allclose(z0[:, ~before], z1[:, ~before])
+
+
+def test_q_is_normalised():
+    # S = 4 (2x2 interior): sum over the 16 interiors of q(x | ring) = 1
+    flat = ol.init_params(11, gain=2.0)
+    ring = rand_windows(5, 4, 9)
+    for b in range(5):
+        total = 0.0
+        for bits in itertools.product([-1, 1], repeat=4):
+            w = ring[b:b + 1].copy()
+            w[0, 1:3, 1:3] = np.array(bits).reshape(2, 2)
+            z, _ = ol.forward(w, flat)
+            total += math.exp(ol.log_q(w, z)[0])
+        assert abs(total - 1.0) < 1e-12
+
+
+def test_local_energy_matches_full_hamiltonian():
+    rng = np.random.default_rng(4)
+    L = 32
+    for trial in range(20):
+        s = np.where(rng.random((L, L)) < 0.5, -1, 1).astype(np.int8)
+        x0, y0 = int(rng.integers(0, L)), int(rng.integers(0, L))
+        w_old = ol.extract(s, x0, y0)
+        new = s.copy()
+        ys, xs = (y0 + np.arange(8)) % L, (x0 + np.arange(8)) % L
+        new[np.ix_(ys, xs)] = np.where(rng.random((8, 8)) < 0.5, -1, 1)
+        w_new = ol.extract(new, x0, y0)
+        assert ol.local_energy(w_new) - ol.local_energy(w_old) == oracle.energy(new) - oracle.energy(s)
+
+
+def test_patch_origins_tile_the_lattice_and_rings_avoid_interiors():
+    L = 64
+    cover = np.zeros((L, L), int)
+    for r in range(4):
+        inter = np.zeros((L, L), int)
+        ring = np.zeros((L, L), int)
+        for (x0, y0) in ol.patch_origins(L, r):
+            ys, xs = (y0 + np.arange(8)) % L, (x0 + np.arange(8)) % L
+            inter[np.ix_(ys, xs)] += 1
+            ys2, xs2 = (y0 - 1 + np.arange(10)) % L, (x0 - 1 + np.arange(10)) % L
+            ring[np.ix_(ys2, xs2)] += 1
+        ring -= inter
+        assert inter.max() == 1
+        assert (ring[inter > 0] == 0).all()          # no ring site is another patch's interior
+        cover += inter
+    assert (cover == 1).all()                          # four rounds cover every site once
+
+
+def test_detailed_balance_exact_on_4x4_torus():
+    """One patch move (2x2 interior, its ring = the rest of a 4x4 torus):
+    pi(s) P(s -> s') = pi(s') P(s' -> s) for every pair, all 2^16 states."""
+    T = 2.3
+    flat = ol.init_params(21, gain=2.5)
+    rings = np.array(list(itertools.product([-1, 1], repeat=12)), dtype=np.int8)   # 4096 rings
+    inter = np.array(list(itertools.product([-1, 1], repeat=4)), dtype=np.int8)    # 16 interiors
+    ring_pos = [(r, c) for r in range(4) for c in range(4) if not (1 <= r <= 2 and 1 <= c <= 2)]
+    W = np.zeros((4096, 16, 4, 4), np.int8)
+    for k, (r, c) in enumerate(ring_pos):
+        W[:, :, r, c] = rings[:, k][:, None]
+    W[:, :, 1:3, 1:3] = inter.reshape(16, 2, 2)[None]
+    flatW = W.reshape(-1, 4, 4)
+    z, _ = ol.forward(flatW, flat)
+    lq = ol.log_q(flatW, z).reshape(4096, 16)
+    E = ol.local_energy(flatW).reshape(4096, 16)
+    # full energy = local + ring-ring bonds (same for all interiors of a ring): pi ~ exp(-E_local/T) per ring
+    for b in range(0, 4096, 37):
+        for i in range(16):
+            for j in range(16):
+                if i == j:
+                    continue
+                la_ij = ol.log_acceptance(int(E[b, j] - E[b, i]), lq[b, i], lq[b, j], T)
+                la_ji = ol.log_acceptance(int(E[b, i] - E[b, j]), lq[b, j], lq[b, i], T)
+                flow_ij = -E[b, i] / T + lq[b, j] + min(0.0, la_ij)
+                flow_ji = -E[b, j] / T + lq[b, i] + min(0.0, la_ji)
+                assert abs(flow_ij - flow_ji) < 1e-9
+
+
+def test_adam_first_step_is_signed_lr():
+    g = np.array([0.5, -2.0, 1e-3, 0.0], np.float32)
+    p, m, v = ol.adam_step(np.zeros(4, np.float32), np.zeros(4, np.float32), np.zeros(4, np.float32), g, 1, 0.01)
+    assert np.allclose(p[:3], -0.01 * np.sign(g[:3]), rtol=1e-4) and p[3] == 0.0
+
+
+def test_learned_round_runs_and_keeps_energy_bookkeeping():
+    L, T, seed = 32, 2.3, 3
+    s = oracle.init(L, seed, 0)
+    e0, m0 = oracle.energy(s), oracle.magnetization(s)
+    flat = ol.init_params(1, gain=0.5)
+    acc, dE, dM, recs = ol.learned_round(s, flat, T, seed, 0, 0)
+    assert len(recs) == (L // 16) ** 2
+    assert oracle.energy(s) - e0 == dE and oracle.magnetization(s) - m0 == dM
+    assert acc == sum(r["accept"] for r in recs)
