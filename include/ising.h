@@ -222,6 +222,88 @@ int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_it
  * captured for that n (1 = on, 0 = off).  Results are identical either way. */
 int ising_set_graph(ising_t h, int on);
 
+/* Copy the packed spins of every lattice (the handle's whole spin array, sum of
+ * L*L/8 bytes, lattices one after another) to dev_dst on the handle's stream;
+ * bytes must be at least that size.  Used to collect training snapshots. */
+int ising_snapshot(ising_t h, void* dev_dst, size_t bytes);
+
+/* ------------------------------------------------------------------------
+ * Learned patch proposal.  The paper has no learned component; it motivates
+ * improving on local moves by the critical slowing down of single-site
+ * updates near T_c (Section 1).  Definitions:
+ *
+ * Window: an 8x8 interior patch plus its one-site ring, 10x10 spins (+1/-1,
+ * int8, row-major), positions p = (r, c) in raster order; interior =
+ * 1 <= r, c <= 8.
+ * Net (ISING_NET_PARAMS fp32 parameters, flat order W1[16][16], b1[16],
+ * W2[5][16][16], b2[16], W3[5][16][16], b3[16], W4[5][16], b4[1]): a masked
+ * 3x3-convolution autoregressive model with 16 channels.  Layer 1 reads 16
+ * features per position: the interior spins at the 4 taps before p in raster
+ * order, (dy,dx) in {(-1,-1),(-1,0),(-1,1),(0,-1)}, the ring spins at the 9
+ * taps (dy,dx) in {-1,0,1}^2 (row-major), then 3 zeros (positions outside the
+ * window read 0).  Layers 2, 3 (16 -> 16) and 4 (16 -> 1) sum over the 5 taps
+ * {(-1,-1),(-1,0),(-1,1),(0,-1),(0,0)}; W[t][ci][co].  Hidden activations are
+ * bf16(relu(.)), weights enter as bf16, sums are fp32 (tensor cores).  z(p) is
+ * the logit of P(spin = +1) at interior p given the ring and earlier interior
+ * spins; log q(window) = sum over interior p of log sigmoid(s_p z(p)) (fp32).
+ * Sampling: s_p = +1 iff r_p < floor(2^32 sigmoid(z(p))) (sigmoid in fp32),
+ * r_p = lane i%4 of Philox counter (16 j + i/4, round, s, 4), i = 8(r-1)+(c-1),
+ * j the patch index, key = the lattice seed.
+ * Round (ising_learned_round): patches with interior top-left site
+ * (16a + ox, 16b + oy), a, b in [0, L/16), patch index j = b L/16 + a,
+ * (ox, oy) = (0,0), (8,8), (0,8), (8,0) for round % 4 = 0..3; every ring
+ * avoids every other interior, so all patches move at once.  Each patch
+ * proposes x' ~ q(. | ring), accepted iff log u < log alpha with
+ * log alpha = -dE/T + log q(x) - log q(x') in FP64 (dE over the bonds touching
+ * the interior) and u = ((r0 >> 5) 2^26 + (r1 >> 6) + 0.5) / 2^53 from lanes
+ * 0, 1 of Philox counter (j, round, s, 5).  E and M are updated exactly.
+ * ------------------------------------------------------------------------ */
+#define ISING_NET_PARAMS 2945
+typedef struct ising_net* ising_net_t;
+
+/* Device workspace of a net that handles up to max_windows windows per call
+ * (training batch, or patches of one round: sum over lattices of (L/16)^2) and
+ * rounds over up to max_lattices lattices. */
+int ising_net_workspace_bytes(int max_windows, int max_lattices, size_t* bytes);
+int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* dev_workspace,
+                     size_t ws_bytes, void* cuda_stream);
+void ising_net_destroy(ising_net_t net);
+
+/* fp32 parameters in/out (host, ISING_NET_PARAMS); set also zeroes the Adam
+ * moments and its step count. */
+int ising_net_set_params(ising_net_t net, const float* host_params);
+int ising_net_get_params(ising_net_t net, float* host_params);
+
+/* Teacher-forced scoring of n host windows: log q per window (host [n]) and,
+ * if host_z is not NULL, the logits of all 100 positions (host [n][100]). */
+int ising_net_score(ising_net_t net, const int8_t* host_windows, int n, float* host_logq, float* host_z);
+
+/* Sample the interiors of n host windows given their rings (in place) with
+ * keys[4*w + 0..3] = (key0, key1, s, j) and the round index; log q of the
+ * samples to host_logq [n]. */
+int ising_net_sample(ising_net_t net, int8_t* host_windows, int n, const uint32_t* host_keys,
+                     uint32_t round_index, float* host_logq);
+
+/* Gradient of the mean negative log-likelihood of n host windows (host
+ * [ISING_NET_PARAMS]) and that loss; does not change the parameters. */
+int ising_net_grad(ising_net_t net, const int8_t* host_windows, int n, float* host_grad, float* host_loss);
+
+/* Train with Adam (lr; beta1 0.9, beta2 0.999, eps 1e-8): each step draws
+ * `batch` windows from n_snap packed L x L lattices at dev_pool_words (one
+ * after another, L*L/32 words each; e.g. snapshots taken with
+ * ising_lattice_words) -- window b of step s takes snapshot r.x % n_snap and
+ * top-left interior site (r.y % L, r.z % L), r = Philox counter (b, step, 0,
+ * 6) keyed by seed -- then runs forward, backward and the update.  The
+ * per-step losses go to host_losses [steps] if not NULL. */
+int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int L, int64_t steps,
+                    int batch, float lr, uint64_t seed, float* host_losses);
+
+/* One learned patch round over every lattice of h (round index round_index;
+ * L must be a multiple of 16, which every valid L is).  Accepted patches per
+ * lattice go to host_accepted [n_sims] if not NULL.  The handle's sweep
+ * counter is unchanged; its current E and M are updated. */
+int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t* host_accepted);
+
 /* Allocation-free streaming sweep.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code running
  * inside a host application that owns all device memory through its own pool,

@@ -252,21 +252,40 @@ def u53(r0, r1):
     return (float((int(r0) >> 5) * 67108864 + (int(r1) >> 6)) + 0.5) / 9007199254740992.0
 
 
-def sample(win_ring, flat, uniforms):
+def sample_threshold(z):
+    """floor(2^32 sigmoid(z)) with the sigmoid evaluated in float32 (the
+    precision the sampling decision is defined in); 2^32 - 1 if it rounds to 1."""
+    z32 = np.asarray(z, dtype=np.float32)
+    with np.errstate(over="ignore"):
+        s32 = np.float32(1.0) / (np.float32(1.0) + np.exp(-z32))
+    t = np.floor(s32.astype(np.float64) * 4294967296.0)
+    return np.where(s32 >= np.float32(1.0), 4294967295.0, t)
+
+
+def sample(win_ring, flat, R):
     """Autoregressive sample of the interior given the ring.  win_ring:
-    [B, S, S] (interior values ignored), uniforms [B, P*P] in (0,1).  Returns
-    (x' windows, log q(x')).  x'_p = +1 iff u_p < sigmoid(z_p)."""
+    [B, S, S] (interior values ignored), R [B, P*P] raw u32 draws in raster
+    order.  x'_p = +1 iff R_p < floor(2^32 sigmoid(z_p)).  Returns (windows,
+    log q(x'), per-site thresholds)."""
     w = np.array(win_ring, dtype=np.float64)
     B, S, _ = w.shape
     P = S - 2
     w[:, 1:S - 1, 1:S - 1] = 0.0
+    thr = np.zeros((B, P * P))
     for i in range(P * P):
         r, c = 1 + i // P, 1 + i % P
         z, _ = forward(w, flat)
-        pz = 1.0 / (1.0 + np.exp(-z[:, r, c]))
-        w[:, r, c] = np.where(uniforms[:, i] < pz, 1.0, -1.0)
+        thr[:, i] = sample_threshold(z[:, r, c])
+        w[:, r, c] = np.where(np.asarray(R[:, i], np.float64) < thr[:, i], 1.0, -1.0)
     z, _ = forward(w, flat)
-    return w.astype(np.int8), log_q(w, z)
+    return w.astype(np.int8), log_q(w, z), thr
+
+
+def sampling_draws(seed, s, j, round_index, P=8):
+    """The raw u32 draws of patch j: lane i % 4 of Philox counter
+    (16 j + i/4, round, s, 4), i.e. rank p = 64 j + i."""
+    import oracle
+    return np.array([oracle.site_random(seed, 64 * j + i, round_index, s, 4) for i in range(P * P)], np.float64)
 
 
 def learned_round(sigma, flat, T, seed, s, round_index, P=8):
@@ -280,12 +299,8 @@ def learned_round(sigma, flat, T, seed, s, round_index, P=8):
     wins = np.stack([extract(sigma, x0, y0, P) for (x0, y0) in origins])
     z, _ = forward(wins, flat)
     lq_old = log_q(wins, z)
-    nP = P * P
-    U = np.zeros((len(origins), nP))
-    for j in range(len(origins)):
-        for i in range(nP):
-            U[j, i] = u32_to_unit(oracle.site_random(seed, 16 * j * 4 + i, round_index, s, 4))
-    new, lq_new = sample(wins, flat, U)
+    R = np.stack([sampling_draws(seed, s, j, round_index, P) for j in range(len(origins))])
+    new, lq_new, thr = sample(wins, flat, R)
     dE = local_energy(new) - local_energy(wins)
     acc = 0
     dEt = dMt = 0
@@ -297,6 +312,7 @@ def learned_round(sigma, flat, T, seed, s, round_index, P=8):
         u = u53(r0, r1)
         ok = math.log(u) < log_alpha
         recs.append({"j": j, "log_alpha": log_alpha, "u": u, "accept": ok, "new": new[j], "old": wins[j],
+                     "draws": R[j], "thr": thr[j],
                      "lq_old": float(lq_old[j]), "lq_new": float(lq_new[j]), "dE": int(dE[j])})
         if ok:
             acc += 1

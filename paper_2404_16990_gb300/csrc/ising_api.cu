@@ -609,6 +609,16 @@ int ising_lattice_words(ising_t h, int sim, void** dev_words, size_t* n_words) {
     return ISING_OK;
 }
 
+int ising_snapshot(ising_t h, void* dev_dst, size_t bytes) {
+    if (!h || !dev_dst) return fail(ISING_EINVAL, "NULL argument");
+    if (bytes < h->layout.spin_bytes) return fail(ISING_EINVAL, "destination too small (%zu < %zu)", bytes,
+                                                  h->layout.spin_bytes);
+    if (h->n == 0) return ISING_OK;
+    CUDA_TRY(cudaMemcpyAsync(dev_dst, h->st.spins, h->layout.spin_bytes, cudaMemcpyDeviceToDevice, h->stream),
+             "snapshot");
+    return ISING_OK;
+}
+
 int ising_get_thresholds(ising_t h, uint32_t* thr) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (h->n == 0) return ISING_OK;
@@ -901,6 +911,251 @@ void ising_destroy(ising_t h) {
     cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     delete h;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Learned patch proposal: network handle and round
+// ===========================================================================
+struct ising_net {
+    int max_windows = 0, max_lattices = 0;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    NetState ns{};
+    int8_t* win = nullptr;
+    int8_t* win2 = nullptr;
+    float* z = nullptr;
+    float* lq = nullptr;
+    float* lq2 = nullptr;
+    __nv_bfloat16* h = nullptr;
+    LearnedKey* keys = nullptr;
+    LearnedLat* ll = nullptr;
+    unsigned long long* accepted = nullptr;
+    int step = 0;
+};
+
+namespace {
+
+struct NetLayout {
+    size_t w, m, v, g, wb, loss, win, win2, z, lq, lq2, h, keys, ll, acc, total;
+};
+
+NetLayout net_layout(int W, int NL) {
+    NetLayout l{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t P = ISING_NET_PARAMS, w = (size_t)W;
+    l.w = take(P * 4); l.m = take(P * 4); l.v = take(P * 4); l.g = take(P * 4); l.wb = take(P * 2);
+    l.loss = take(16);
+    l.win = take(w * 100); l.win2 = take(w * 100);
+    l.z = take(w * 100 * 4);
+    l.lq = take(w * 4); l.lq2 = take(w * 4);
+    l.h = take(3 * w * 100 * 16 * 2);
+    l.keys = take(w * sizeof(LearnedKey));
+    l.ll = take((size_t)NL * sizeof(LearnedLat));
+    l.acc = take((size_t)NL * 8);
+    l.total = off;
+    return l;
+}
+
+int net_upload_windows(ising_net* net, const int8_t* host, int n) {
+    if (n < 1 || n > net->max_windows) return fail(ISING_EINVAL, "n must be in [1, max_windows=%d]", net->max_windows);
+    if (!host) return fail(ISING_EINVAL, "windows is NULL");
+    for (size_t i = 0; i < (size_t)n * 100; ++i)
+        if (host[i] != 1 && host[i] != -1) return fail(ISING_EINVAL, "window spins must be +1/-1");
+    CUDA_TRY(cudaMemcpyAsync(net->win, host, (size_t)n * 100, cudaMemcpyHostToDevice, net->stream), "upload windows");
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_net_workspace_bytes(int max_windows, int max_lattices, size_t* bytes) {
+    if (!bytes || max_windows < 1 || max_lattices < 1)
+        return fail(ISING_EINVAL, "max_windows and max_lattices must be >= 1");
+    *bytes = net_layout(max_windows, max_lattices).total;
+    return ISING_OK;
+}
+
+int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* dev_ws, size_t ws_bytes,
+                     void* cuda_stream) {
+    if (!out) return fail(ISING_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_windows < 1 || max_lattices < 1) return fail(ISING_EINVAL, "max_windows and max_lattices must be >= 1");
+    const NetLayout l = net_layout(max_windows, max_lattices);
+    if (ws_bytes < l.total) return fail(ISING_ENOMEM, "net workspace too small: %zu < %zu", ws_bytes, l.total);
+    if (!dev_ws || ((uintptr_t)dev_ws) % kAlign) return fail(ISING_EINVAL, "workspace NULL or not 256-byte aligned");
+    CUDA_TRY(configure_learned_kernels(), "configure learned kernels");
+    auto* net = new ising_net();
+    char* b = (char*)dev_ws;
+    net->max_windows = max_windows;
+    net->max_lattices = max_lattices;
+    net->stream = (cudaStream_t)cuda_stream;
+    net->ws = b;
+    net->ns = NetState{(float*)(b + l.w), (float*)(b + l.m), (float*)(b + l.v), (float*)(b + l.g),
+                       (__nv_bfloat16*)(b + l.wb), (float*)(b + l.loss)};
+    net->win = (int8_t*)(b + l.win);
+    net->win2 = (int8_t*)(b + l.win2);
+    net->z = (float*)(b + l.z);
+    net->lq = (float*)(b + l.lq);
+    net->lq2 = (float*)(b + l.lq2);
+    net->h = (__nv_bfloat16*)(b + l.h);
+    net->keys = (LearnedKey*)(b + l.keys);
+    net->ll = (LearnedLat*)(b + l.ll);
+    net->accepted = (unsigned long long*)(b + l.acc);
+    cudaError_t e = cudaMemsetAsync(b, 0, l.total, net->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) { delete net; return cuda_fail(e, "net create"); }
+    *out = net;
+    return ISING_OK;
+}
+
+void ising_net_destroy(ising_net_t net) {
+    if (!net) return;
+    cudaStreamSynchronize(net->stream);
+    delete net;
+}
+
+int ising_net_set_params(ising_net_t net, const float* host) {
+    if (!net || !host) return fail(ISING_EINVAL, "NULL argument");
+    for (int i = 0; i < ISING_NET_PARAMS; ++i)
+        if (!std::isfinite(host[i])) return fail(ISING_EINVAL, "parameter %d is not finite", i);
+    const size_t nb = ISING_NET_PARAMS * sizeof(float);
+    CUDA_TRY(cudaMemcpyAsync(net->ns.w, host, nb, cudaMemcpyHostToDevice, net->stream), "set params");
+    CUDA_TRY(cudaMemsetAsync(net->ns.m, 0, nb, net->stream), "zero m");
+    CUDA_TRY(cudaMemsetAsync(net->ns.v, 0, nb, net->stream), "zero v");
+    CUDA_TRY(launch_to_bf16(net->ns, net->stream), "bf16 copy");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    net->step = 0;
+    return ISING_OK;
+}
+
+int ising_net_get_params(ising_net_t net, float* host) {
+    if (!net || !host) return fail(ISING_EINVAL, "NULL argument");
+    CUDA_TRY(cudaMemcpyAsync(host, net->ns.w, ISING_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, net->stream),
+             "get params");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_net_score(ising_net_t net, const int8_t* host_windows, int n, float* host_logq, float* host_z) {
+    if (!net || !host_logq) return fail(ISING_EINVAL, "NULL argument");
+    int rc = net_upload_windows(net, host_windows, n);
+    if (rc != ISING_OK) return rc;
+    CUDA_TRY(launch_net_forward(net->ns, net->win, n, net->lq, host_z ? net->z : nullptr, nullptr, net->stream),
+             "score");
+    CUDA_TRY(cudaMemcpyAsync(host_logq, net->lq, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream), "copy logq");
+    if (host_z)
+        CUDA_TRY(cudaMemcpyAsync(host_z, net->z, (size_t)n * 400, cudaMemcpyDeviceToHost, net->stream), "copy z");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_net_sample(ising_net_t net, int8_t* host_windows, int n, const uint32_t* host_keys, uint32_t round_index,
+                     float* host_logq) {
+    if (!net || !host_keys || !host_logq) return fail(ISING_EINVAL, "NULL argument");
+    int rc = net_upload_windows(net, host_windows, n);
+    if (rc != ISING_OK) return rc;
+    CUDA_TRY(cudaMemcpyAsync(net->keys, host_keys, (size_t)n * sizeof(LearnedKey), cudaMemcpyHostToDevice,
+                             net->stream), "upload keys");
+    CUDA_TRY(launch_net_sample(net->ns, net->win, n, net->lq, net->keys, round_index, net->stream), "sample");
+    CUDA_TRY(cudaMemcpyAsync(host_windows, net->win, (size_t)n * 100, cudaMemcpyDeviceToHost, net->stream),
+             "copy windows");
+    CUDA_TRY(cudaMemcpyAsync(host_logq, net->lq, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream), "copy logq");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_net_grad(ising_net_t net, const int8_t* host_windows, int n, float* host_grad, float* host_loss) {
+    if (!net || !host_grad) return fail(ISING_EINVAL, "NULL argument");
+    int rc = net_upload_windows(net, host_windows, n);
+    if (rc != ISING_OK) return rc;
+    CUDA_TRY(cudaMemsetAsync(net->ns.g, 0, ISING_NET_PARAMS * sizeof(float), net->stream), "zero grad");
+    CUDA_TRY(cudaMemsetAsync(net->ns.loss, 0, sizeof(float), net->stream), "zero loss");
+    CUDA_TRY(launch_net_forward(net->ns, net->win, n, net->lq, net->z, net->h, net->stream), "forward");
+    CUDA_TRY(launch_net_backward(net->ns, net->win, n, net->z, net->h, net->ns.g, net->ns.loss, net->stream),
+             "backward");
+    CUDA_TRY(cudaMemcpyAsync(host_grad, net->ns.g, ISING_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost,
+                             net->stream), "copy grad");
+    if (host_loss)
+        CUDA_TRY(cudaMemcpyAsync(host_loss, net->ns.loss, sizeof(float), cudaMemcpyDeviceToHost, net->stream),
+                 "copy loss");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int L, int64_t steps, int batch,
+                    float lr, uint64_t seed, float* host_losses) {
+    if (!net || !dev_pool_words) return fail(ISING_EINVAL, "NULL argument");
+    if (n_snap < 1 || !valid_L(L)) return fail(ISING_EINVAL, "need n_snap >= 1 and a valid L");
+    if (batch < 1 || batch > net->max_windows) return fail(ISING_EINVAL, "batch must be in [1, %d]", net->max_windows);
+    if (steps < 0 || !(lr > 0.f) || !std::isfinite(lr)) return fail(ISING_EINVAL, "invalid steps or lr");
+    std::vector<float> losses;
+    for (int64_t s = 0; s < steps; ++s) {
+        const uint32_t step_id = (uint32_t)(net->step);
+        CUDA_TRY(launch_train_windows((const uint32_t*)dev_pool_words, n_snap, (uint32_t)L, batch, seed, step_id,
+                                      net->win, net->stream), "training windows");
+        CUDA_TRY(cudaMemsetAsync(net->ns.g, 0, ISING_NET_PARAMS * sizeof(float), net->stream), "zero grad");
+        CUDA_TRY(cudaMemsetAsync(net->ns.loss, 0, sizeof(float), net->stream), "zero loss");
+        CUDA_TRY(launch_net_forward(net->ns, net->win, batch, net->lq, net->z, net->h, net->stream), "forward");
+        CUDA_TRY(launch_net_backward(net->ns, net->win, batch, net->z, net->h, net->ns.g, net->ns.loss, net->stream),
+                 "backward");
+        net->step += 1;
+        CUDA_TRY(launch_adam(net->ns, lr, net->step, net->stream), "adam");
+        if (host_losses)
+            CUDA_TRY(cudaMemcpyAsync(host_losses + s, net->ns.loss, sizeof(float), cudaMemcpyDeviceToHost,
+                                     net->stream), "copy loss");
+    }
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    return ISING_OK;
+}
+
+int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t* host_accepted) {
+    if (!h || !net) return fail(ISING_EINVAL, "NULL handle");
+    if (round_index < 0 || round_index > (int64_t)0xFFFFFFFFll) return fail(ISING_EINVAL, "round_index out of range");
+    if (h->n == 0) return ISING_OK;
+    if (h->n > net->max_lattices) return fail(ISING_EINVAL, "handle has %d lattices, net allows %d", h->n, net->max_lattices);
+    std::vector<LearnedLat> ll(h->n);
+    int64_t nwin = 0;
+    for (int i = 0; i < h->n; ++i) {
+        LearnedLat d{};
+        d.word_off = h->layout.word_off[i];
+        d.L = (uint32_t)h->L[i];
+        d.lat = (uint32_t)i;
+        d.sim = (uint32_t)i;
+        d.key0 = (uint32_t)(h->seed[i] & 0xFFFFFFFFull);
+        d.key1 = (uint32_t)(h->seed[i] >> 32);
+        d.patch_begin = (uint32_t)nwin;
+        d.beta = 1.0 / h->T[i];
+        ll[i] = d;
+        nwin += (int64_t)(h->L[i] / 16) * (h->L[i] / 16);
+    }
+    if (nwin > net->max_windows) return fail(ISING_EINVAL, "round needs %lld windows, net allows %d",
+                                             (long long)nwin, net->max_windows);
+    static const uint32_t off[4][2] = {{0, 0}, {8, 8}, {0, 8}, {8, 0}};
+    const uint32_t ox = off[round_index % 4][0], oy = off[round_index % 4][1];
+    const uint32_t rt = (uint32_t)round_index;
+    CUDA_TRY(cudaMemcpyAsync(net->ll, ll.data(), ll.size() * sizeof(LearnedLat), cudaMemcpyHostToDevice, h->stream),
+             "upload lattice table");
+    CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
+    CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, (int)nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
+             "gather patches");
+    CUDA_TRY(launch_net_forward(net->ns, net->win, (int)nwin, net->lq, nullptr, nullptr, h->stream), "score");
+    CUDA_TRY(launch_net_sample(net->ns, net->win2, (int)nwin, net->lq2, net->keys, rt, h->stream), "sample");
+    CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, (int)nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
+                             net->accepted, h->stream), "accept");
+    if (host_accepted) {
+        std::vector<unsigned long long> acc(h->n);
+        CUDA_TRY(cudaMemcpyAsync(acc.data(), net->accepted, (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream),
+                 "copy counters");
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+        for (int i = 0; i < h->n; ++i) host_accepted[i] = (int64_t)acc[i];
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");   // the lattice table is a host buffer
+    }
+    return ISING_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,36 @@
+// ising_device.cuh -- device helpers shared by the sweep kernels and the
+// learned-proposal kernels: the Philox4x32-10 counter-based generator.
+#pragma once
+
+#include <cstdint>
+
+namespace ising {
+
+constexpr uint32_t kMulA = 0xD2511F53u;   // Philox4x32 round multipliers
+constexpr uint32_t kMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;  // Philox4x32 key increments
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+// One Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// two 32x32->64 products of counter words 0 and 2 with the multipliers, the
+// new counter being (hi(B c2) ^ c1 ^ k0, lo(B c2), hi(A c0) ^ c3 ^ k1,
+// lo(A c0)), with the key advanced by the increments between rounds.  Counter
+// words 1..3 and the key are usually the same for all sites of a thread, so the
+// compiler hoists their products and the round keys out of per-site loops.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t ka = k0 + (uint32_t)r * kWeylA;
+        const uint32_t kb = k1 + (uint32_t)r * kWeylB;
+        const uint32_t hi_a = __umulhi(kMulA, c0), lo_a = kMulA * c0;
+        const uint32_t hi_b = __umulhi(kMulB, c2), lo_b = kMulB * c2;
+        c0 = hi_b ^ c1 ^ ka;
+        c1 = lo_b;
+        c2 = hi_a ^ c3 ^ kb;
+        c3 = lo_a;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+}  // namespace ising

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace ising {
@@ -65,6 +66,28 @@ struct DevState {
     int n;
 };
 
+// Learned proposal: per-window Philox key of a patch (sampling draws).
+struct LearnedKey {
+    uint32_t key0, key1, sim, j;   // lattice seed (lo, hi), simulation index, patch index
+};
+
+// Learned proposal: per-lattice description for one round.
+struct LearnedLat {
+    uint64_t word_off;     // first word of the lattice
+    uint32_t L, lat, sim, key0, key1, patch_begin;
+    double beta;           // 1 / T
+};
+
+// Learned proposal: device pointers of a network (all in the net workspace).
+struct NetState {
+    float* w;              // fp32 master parameters [ISING_NET_PARAMS]
+    float* m;              // Adam first moments
+    float* v;              // Adam second moments
+    float* g;              // gradient accumulator
+    __nv_bfloat16* wb;     // bf16 copy used by the tensor-core kernels
+    float* loss;           // scalar
+};
+
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_init_random(const DevState& st, int n_lat, cudaStream_t stream);
 cudaError_t launch_observables(const DevState& st, int n_lat, const uint32_t* lat_list,
@@ -79,6 +102,25 @@ cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream)
 
 // Record a message for ising_last_error() and return code (ising_api.cu).
 int set_last_error(int code, const char* msg);
+
+// Learned-proposal launch wrappers (ising_learned.cu).
+cudaError_t configure_learned_kernels();
+cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
+                               __nv_bfloat16* h, cudaStream_t stream);
+cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
+                              uint32_t round_t, cudaStream_t stream);
+cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, const float* z,
+                                const __nv_bfloat16* h, float* grad, float* loss, cudaStream_t stream);
+cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream);
+cudaError_t launch_to_bf16(const NetState& ns, cudaStream_t stream);
+cudaError_t launch_train_windows(const uint32_t* pool, int n_snap, uint32_t L, int nwin, uint64_t seed,
+                                 uint32_t step, int8_t* win, cudaStream_t stream);
+cudaError_t launch_gather_patches(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
+                                  uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys, cudaStream_t stream);
+cudaError_t launch_mh_apply(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
+                            uint32_t oy, const int8_t* win_old, const int8_t* win_new, const float* lq_old,
+                            const float* lq_new, uint32_t round_t, unsigned long long* accepted,
+                            cudaStream_t stream);
 
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);

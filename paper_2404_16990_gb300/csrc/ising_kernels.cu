@@ -16,6 +16,7 @@
 //   word[(c*L + y)*wn + k], bit b <-> site x = 2*(32k + b) + ((y + c) & 1).
 // Bit value 0 = spin +1, 1 = spin -1.
 #include "ising_internal.h"
+#include "ising_device.cuh"
 
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -23,10 +24,6 @@
 namespace ising {
 namespace {
 
-constexpr uint32_t kMulA = 0xD2511F53u;   // Philox4x32 round multipliers
-constexpr uint32_t kMulB = 0xCD9E8D57u;
-constexpr uint32_t kWeylA = 0x9E3779B9u;  // Philox4x32 key increments
-constexpr uint32_t kWeylB = 0xBB67AE85u;
 constexpr int kMaxGroupCount = 256;       // lattices per resident group
 constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
 
@@ -44,25 +41,6 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 
 __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
-}
-
-// One Philox4x32-10 block (Salmon et al. 2011).  Counter words 1..3 and the
-// key are the same for every site of a thread's word, so the compiler hoists
-// their products and the round keys out of the per-word loop.
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t ka = k0 + (uint32_t)r * kWeylA;
-        const uint32_t kb = k1 + (uint32_t)r * kWeylB;
-        const uint32_t hi_a = __umulhi(kMulA, c0), lo_a = kMulA * c0;
-        const uint32_t hi_b = __umulhi(kMulB, c2), lo_b = kMulB * c2;
-        c0 = hi_b ^ c1 ^ ka;
-        c1 = lo_b;
-        c2 = hi_a ^ c3 ^ kb;
-        c3 = lo_a;
-    }
-    return make_uint4(c0, c1, c2, c3);
 }
 
 // Metropolis update of the 32 same-colour spins of word w given the four

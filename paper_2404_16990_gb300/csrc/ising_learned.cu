@@ -1,0 +1,597 @@
+// ising_learned.cu -- learned patch proposal: a masked-convolution
+// autoregressive network over 8x8 patches conditioned on their one-site ring,
+// trained by the library's own forward/backward/Adam kernels, used as an
+// independence proposal accepted by exact Metropolis-Hastings.
+//
+// The paper has no learned component; it motivates improving on local moves by
+// the critical slowing down of single-site updates near T_c (Section 1).  The
+// net, its masks, the move and its random-number keying are defined in
+// include/ising.h (ising_net_* and ising_learned_round).
+//
+// Tensor cores: every layer of the net is a masked 3x3 convolution, i.e. a
+// contraction over (tap, input channel).  The kernels run it as
+// mma.sync.m16n8k16 BF16 x BF16 -> FP32: the M dimension is 16 windows of one
+// warp, K = 16 input channels of one tap (a k-step per tap), N = 16 output
+// channels (two n-tiles).  Positions are visited in raster order, so each
+// window position's activations are computed once, from already final earlier
+// positions: sampling, scoring and the training forward are the same code.
+#include "../../include/ising.h"
+#include "ising_internal.h"
+#include "ising_device.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ising {
+namespace {
+
+constexpr int kS = 10;          // window side
+constexpr int kNPos = kS * kS;  // window positions
+constexpr int kP = 8;           // interior side
+constexpr int kC = 16;          // channels
+constexpr int kSlots = 12;      // activation ring buffer (taps reach 11 positions back)
+constexpr int kOffW1 = 0, kOffB1 = 256, kOffW2 = 272, kOffB2 = 1552, kOffW3 = 1568, kOffB3 = 2848,
+              kOffW4 = 2864, kOffB4 = 2944;
+constexpr int kNParams = ISING_NET_PARAMS;
+static_assert(kOffB4 + 1 == ISING_NET_PARAMS, "parameter layout");
+constexpr int kWarpsFwd = 4;
+// per-warp shared memory of the forward kernel: spins [16][100] int8, then the
+// activation ring [3 layers][12 slots][16 windows][16 channels] bf16
+constexpr int kSpinBytes = 16 * kNPos;                       // 1600
+constexpr int kRingBytes = 3 * kSlots * 16 * kC * 2;          // 18432
+constexpr int kWarpSmem = kSpinBytes + kRingBytes;            // 20032 (multiple of 16)
+
+// (dy, dx) of the "mask B" taps and of the layer-1 features
+__constant__ int8_t c_tapB[5][2] = {{-1, -1}, {-1, 0}, {-1, 1}, {0, -1}, {0, 0}};
+__constant__ int8_t c_feat[16][3] = {
+    // dy, dx, kind (0 = interior spin, 1 = ring spin, 2 = zero)
+    {-1, -1, 0}, {-1, 0, 0}, {-1, 1, 0}, {0, -1, 0},
+    {-1, -1, 1}, {-1, 0, 1}, {-1, 1, 1}, {0, -1, 1}, {0, 0, 1}, {0, 1, 1}, {1, -1, 1}, {1, 0, 1}, {1, 1, 1},
+    {0, 0, 2}, {0, 0, 2}, {0, 0, 2}};
+
+__device__ __forceinline__ bool interior(int r, int c) { return r >= 1 && r <= kP && c >= 1 && c <= kP; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float log_sigmoid(float t) {
+    return -(fmaxf(-t, 0.0f) + log1pf(expf(-fabsf(t))));
+}
+
+// B fragment of a K x N = 16 x 8 slice of a row-major [k][n] bf16 matrix
+// (row stride ld): k = 2*(lane%4) + {0,1} and +8, n = lane/4.
+__device__ __forceinline__ void load_b(const __nv_bfloat16* m, int ld, int n0, int ncols, uint32_t (&b)[2]) {
+    const int lane = threadIdx.x & 31, k = 2 * (lane & 3), n = n0 + (lane >> 2);
+    auto at = [&](int kk) -> float { return n < ncols ? __bfloat162float(m[kk * ld + n]) : 0.0f; };
+    b[0] = pack_bf16(at(k), at(k + 1));
+    b[1] = pack_bf16(at(k + 8), at(k + 9));
+}
+
+struct NetPtrs {
+    const __nv_bfloat16* wb;  // bf16 copy of the parameters (weights used by the mma)
+    const float* wf;          // fp32 master parameters (biases)
+};
+
+// ---------------------------------------------------------------------------
+// Sequential forward over the 100 window positions for 16 windows per warp.
+// MODE 0 scores given windows (teacher forcing); MODE 1 samples the interior.
+// Writes lq[w] = log q(window w) (fp32 sum), and optionally the logits z[w][p]
+// and the activations h[l][w][p][c] (training).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int8_t* win, int n, float* lq,
+                                                                 float* z_out, __nv_bfloat16* h_out,
+                                                                 const LearnedKey* keys, uint32_t round_t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int w0 = (blockIdx.x * kWarpsFwd + warp) * 16;
+    if (w0 >= n) return;
+    int8_t* sp = reinterpret_cast<int8_t*>(smem + warp * kWarpSmem);
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(smem + warp * kWarpSmem + kSpinBytes);
+    auto H = [&](int layer, int slot, int row) -> __nv_bfloat16* {
+        return ring + ((layer * kSlots + slot) * 16 + row) * kC;
+    };
+    for (int i = lane; i < 16 * kNPos; i += 32) {
+        const int row = i / kNPos;
+        sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
+    }
+    // weights -> B fragments (registers)
+    uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[5][2];
+    load_b(net.wb + kOffW1, kC, 0, kC, bw1[0]);
+    load_b(net.wb + kOffW1, kC, 8, kC, bw1[1]);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        load_b(net.wb + kOffW2 + t * 256, kC, 0, kC, bw2[t][0]);
+        load_b(net.wb + kOffW2 + t * 256, kC, 8, kC, bw2[t][1]);
+        load_b(net.wb + kOffW3 + t * 256, kC, 0, kC, bw3[t][0]);
+        load_b(net.wb + kOffW3 + t * 256, kC, 8, kC, bw3[t][1]);
+        load_b(net.wb + kOffW4 + t * kC, 1, 0, 1, bw4[t]);     // N = 1 (column 0 only)
+    }
+    float bias[3][2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int co = nt * 8 + 2 * tq + e;
+            bias[0][nt][e] = net.wf[kOffB1 + co];
+            bias[1][nt][e] = net.wf[kOffB2 + co];
+            bias[2][nt][e] = net.wf[kOffB3 + co];
+        }
+    const float b4 = net.wf[kOffB4];
+    float lq_acc[2] = {0.0f, 0.0f};
+    __syncwarp();
+
+    for (int p = 0; p < kNPos; ++p) {
+        const int r = p / kS, c = p - r * kS, slot = p % kSlots;
+        // ---- layer 1: features (mask A interior taps + ring taps) ----
+        uint32_t a[4];
+        {
+            float f[2][4];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int8_t* s = sp + (g + 8 * rr) * kNPos;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = 2 * tq + (e & 1) + ((e >> 1) ? 8 : 0);
+                    const int kind = c_feat[k][2];
+                    const int yy = r + c_feat[k][0], xx = c + c_feat[k][1];
+                    float v = 0.0f;
+                    if (kind != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
+                        const bool in = interior(yy, xx);
+                        if ((kind == 0) == in) v = (float)s[yy * kS + xx];
+                    }
+                    f[rr][e] = v;
+                }
+            }
+            a[0] = pack_bf16(f[0][0], f[0][1]);
+            a[1] = pack_bf16(f[1][0], f[1][1]);
+            a[2] = pack_bf16(f[0][2], f[0][3]);
+            a[3] = pack_bf16(f[1][2], f[1][3]);
+        }
+#pragma unroll
+        for (int layer = 0; layer < 3; ++layer) {
+            float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            if (layer == 0) {
+                mma16816(d[0], a, bw1[0]);
+                mma16816(d[1], a, bw1[1]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+                    if (yy < 0 || xx < 0 || xx >= kS) continue;
+                    const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
+                    const __nv_bfloat16* h0 = H(layer - 1, sl, g);
+                    const __nv_bfloat16* h8 = H(layer - 1, sl, g + 8);
+                    uint32_t at[4];
+                    at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
+                    at[1] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq);
+                    at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
+                    at[3] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq + 8);
+                    if (layer == 1) { mma16816(d[0], at, bw2[t][0]); mma16816(d[1], at, bw2[t][1]); }
+                    else { mma16816(d[0], at, bw3[t][0]); mma16816(d[1], at, bw3[t][1]); }
+                }
+            }
+            // bias, relu, bf16 into the ring (and the activation output)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int co = nt * 8 + 2 * tq;
+                const uint32_t v0 = pack_bf16(fmaxf(d[nt][0] + bias[layer][nt][0], 0.f),
+                                              fmaxf(d[nt][1] + bias[layer][nt][1], 0.f));
+                const uint32_t v8 = pack_bf16(fmaxf(d[nt][2] + bias[layer][nt][0], 0.f),
+                                              fmaxf(d[nt][3] + bias[layer][nt][1], 0.f));
+                *reinterpret_cast<uint32_t*>(H(layer, slot, g) + co) = v0;
+                *reinterpret_cast<uint32_t*>(H(layer, slot, g + 8) + co) = v8;
+                if (h_out) {
+                    if (w0 + g < n)
+                        *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g) * kNPos + p) * kC + co) = v0;
+                    if (w0 + g + 8 < n)
+                        *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g + 8) * kNPos + p) * kC + co) = v8;
+                }
+            }
+            __syncwarp();
+        }
+        // ---- layer 4: the logit ----
+        float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+            if (yy < 0 || xx < 0 || xx >= kS) continue;
+            const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
+            const __nv_bfloat16* h0 = H(2, sl, g);
+            const __nv_bfloat16* h8 = H(2, sl, g + 8);
+            uint32_t at[4];
+            at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
+            at[1] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq);
+            at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
+            at[3] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq + 8);
+            mma16816(d4, at, bw4[t]);
+        }
+        if (tq == 0) {   // column 0 of the C fragment: rows g and g + 8
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int row = g + 8 * rr, w = w0 + row;
+                const float z = (rr ? d4[2] : d4[0]) + b4;
+                if (w < n) {
+                    if (z_out) z_out[(size_t)w * kNPos + p] = z;
+                    if (interior(r, c)) {
+                        int8_t x = sp[row * kNPos + p];
+                        if (MODE == 1) {
+                            const LearnedKey k = keys[w];
+                            const int i = (r - 1) * kP + (c - 1);
+                            const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
+                            const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
+                            const float sg = 1.0f / (1.0f + expf(-z));
+                            const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
+                            x = (u < thr) ? (int8_t)1 : (int8_t)-1;
+                            sp[row * kNPos + p] = x;
+                        }
+                        lq_acc[rr] += log_sigmoid((float)x * z);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (tq == 0) {
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int w = w0 + g + 8 * rr;
+            if (w < n) lq[w] = lq_acc[rr];
+        }
+    }
+    if (MODE == 1) {
+        for (int i = lane; i < 16 * kNPos; i += 32) {
+            const int row = i / kNPos;
+            if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward pass (FP32 CUDA cores), one warp per window: gradient of the mean
+// negative log-likelihood through the bf16 weights; weight gradients summed
+// per block in shared memory, then added to `grad`.
+// ---------------------------------------------------------------------------
+constexpr int kWarpsBwd = 4;
+
+__global__ void __launch_bounds__(kWarpsBwd * 32) net_backward_kernel(NetPtrs net, const int8_t* win, int n,
+                                                                      const float* z, const __nv_bfloat16* h,
+                                                                      float* grad, float* loss, float inv_batch) {
+    extern __shared__ __align__(16) float fsm[];
+    float* gacc = fsm;                                          // [kNParams]
+    float* wbuf = fsm + ((kNParams + 3) / 4) * 4;               // per warp: dA [100][16], dH [100][16]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kNParams; i += blockDim.x) gacc[i] = 0.f;
+    __syncthreads();
+    float* dA = wbuf + warp * 2 * kNPos * kC;
+    float* dH = dA + kNPos * kC;
+    float loss_acc = 0.f;
+    auto Wb = [&](int off) { return __bfloat162float(net.wb[off]); };
+
+    for (int w = blockIdx.x * kWarpsBwd + warp; w < n; w += gridDim.x * kWarpsBwd) {
+        const int8_t* x = win + (size_t)w * kNPos;
+        const __nv_bfloat16* H1 = h + ((size_t)0 * n + w) * kNPos * kC;
+        const __nv_bfloat16* H2 = h + ((size_t)1 * n + w) * kNPos * kC;
+        const __nv_bfloat16* H3 = h + ((size_t)2 * n + w) * kNPos * kC;
+        // dz (stored in dA[p][0])
+        for (int p = lane; p < kNPos; p += 32) {
+            const int r = p / kS, c = p % kS;
+            float dz = 0.f;
+            if (interior(r, c)) {
+                const float zz = z[(size_t)w * kNPos + p], xv = (float)x[p];
+                dz = (1.0f / (1.0f + expf(-zz)) - 0.5f * (xv + 1.0f)) * inv_batch;
+                loss_acc -= log_sigmoid(xv * zz) * inv_batch;
+            }
+            dA[p * kC] = dz;
+        }
+        __syncwarp();
+        // layer 4: dW4, db4, dH3
+        for (int e = lane; e < 5 * kC; e += 32) {
+            const int t = e / kC, ci = e % kC;
+            float s = 0.f;
+            for (int p = 0; p < kNPos; ++p) {
+                const int r = p / kS, c = p % kS, yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+                if (!interior(r, c) || yy < 0 || xx < 0 || xx >= kS) continue;
+                s += dA[p * kC] * __bfloat162float(H3[(yy * kS + xx) * kC + ci]);
+            }
+            atomicAdd(&gacc[kOffW4 + e], s);
+        }
+        if (lane == 0) {
+            float s = 0.f;
+            for (int p = 0; p < kNPos; ++p) s += dA[p * kC];
+            atomicAdd(&gacc[kOffB4], s);
+        }
+        for (int e = lane; e < kNPos * kC; e += 32) {
+            const int q = e / kC, ci = e % kC, qr = q / kS, qc = q % kS;
+            float s = 0.f;
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                const int pr = qr - c_tapB[t][0], pc = qc - c_tapB[t][1];
+                if (pr < 0 || pr >= kS || pc < 0 || pc >= kS || !interior(pr, pc)) continue;
+                s += Wb(kOffW4 + t * kC + ci) * dA[(pr * kS + pc) * kC];
+            }
+            dH[e] = (__bfloat162float(H3[e]) > 0.f) ? s : 0.f;   // dA3
+        }
+        __syncwarp();
+        // layers 3 and 2: dW, db, dA of the layer below
+        for (int layer = 3; layer >= 2; --layer) {
+            const __nv_bfloat16* Hin = (layer == 3) ? H2 : H1;
+            const int offW = (layer == 3) ? kOffW3 : kOffW2, offB = (layer == 3) ? kOffB3 : kOffB2;
+            const float* dAl = dH;      // dA of this layer
+            float* dAn = dA;            // dA of the layer below (overwrites the buffer)
+            for (int e = lane; e < 5 * kC * kC; e += 32) {
+                const int t = e / (kC * kC), ci = (e / kC) % kC, co = e % kC;
+                float s = 0.f;
+                for (int p = 0; p < kNPos; ++p) {
+                    const int r = p / kS, c = p % kS, yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+                    if (yy < 0 || xx < 0 || xx >= kS) continue;
+                    s += dAl[p * kC + co] * __bfloat162float(Hin[(yy * kS + xx) * kC + ci]);
+                }
+                atomicAdd(&gacc[offW + e], s);
+            }
+            if (lane < kC) {
+                float s = 0.f;
+                for (int p = 0; p < kNPos; ++p) s += dAl[p * kC + lane];
+                atomicAdd(&gacc[offB + lane], s);
+            }
+            __syncwarp();
+            for (int e = lane; e < kNPos * kC; e += 32) {
+                const int q = e / kC, ci = e % kC, qr = q / kS, qc = q % kS;
+                float s = 0.f;
+                for (int t = 0; t < 5; ++t) {
+                    const int pr = qr - c_tapB[t][0], pc = qc - c_tapB[t][1];
+                    if (pr < 0 || pr >= kS || pc < 0 || pc >= kS) continue;
+                    const float* dap = dAl + (pr * kS + pc) * kC;
+                    const int wo = offW + t * kC * kC + ci * kC;
+#pragma unroll 4
+                    for (int co = 0; co < kC; ++co) s += Wb(wo + co) * dap[co];
+                }
+                dAn[e] = (__bfloat162float(Hin[e]) > 0.f) ? s : 0.f;
+            }
+            __syncwarp();
+            // move dA of the layer below into dH for the next iteration
+            for (int e = lane; e < kNPos * kC; e += 32) dH[e] = dAn[e];
+            __syncwarp();
+        }
+        // layer 1: dW1, db1 from the features
+        for (int e = lane; e < 13 * kC; e += 32) {
+            const int k = e / kC, co = e % kC;
+            const int kind = c_feat[k][2];
+            float s = 0.f;
+            for (int p = 0; p < kNPos; ++p) {
+                const int r = p / kS, c = p % kS, yy = r + c_feat[k][0], xx = c + c_feat[k][1];
+                if (yy < 0 || yy >= kS || xx < 0 || xx >= kS) continue;
+                if ((kind == 0) != interior(yy, xx)) continue;
+                s += dH[p * kC + co] * (float)x[yy * kS + xx];
+            }
+            atomicAdd(&gacc[kOffW1 + e], s);
+        }
+        if (lane < kC) {
+            float s = 0.f;
+            for (int p = 0; p < kNPos; ++p) s += dH[p * kC + lane];
+            atomicAdd(&gacc[kOffB1 + lane], s);
+        }
+        __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_down_sync(0xffffffffu, loss_acc, o);
+    if (lane == 0) atomicAdd(loss, loss_acc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNParams; i += blockDim.x)
+        if (gacc[i] != 0.f) atomicAdd(&grad[i], gacc[i]);
+}
+
+// Adam (Kingma & Ba 2015) on the fp32 masters, then refresh the bf16 copy.
+__global__ void adam_kernel(float* w, float* m, float* v, const float* g, __nv_bfloat16* wb, float lr,
+                            float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void to_bf16_kernel(const float* w, __nv_bfloat16* wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNParams) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// spin at (x, y) of a packed lattice (layout of include/ising.h)
+__device__ __forceinline__ int8_t packed_spin(const uint32_t* base, uint32_t L, uint32_t x, uint32_t y) {
+    const uint32_t wn = L >> 6, c = (x + y) & 1u, j = x >> 1;
+    const uint32_t w = base[((size_t)c * L + y) * wn + (j >> 5)];
+    return ((w >> (j & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
+}
+
+// Training windows: window b's snapshot, and the (x, y) of its top-left
+// interior site, from Philox (counter (b, step, 0, 6), key = seed).
+__global__ void train_windows_kernel(const uint32_t* pool, int n_snap, uint32_t L, int nwin, uint32_t seed_lo,
+                                     uint32_t seed_hi, uint32_t step, int8_t* win) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nwin * kNPos; i += gridDim.x * blockDim.x) {
+        const int b = i / kNPos, p = i % kNPos;
+        const uint4 r = philox((uint32_t)b, step, 0u, 6u, seed_lo, seed_hi);
+        const uint32_t snap = r.x % (uint32_t)n_snap, x0 = r.y % L, y0 = r.z % L;
+        const uint32_t* base = pool + (size_t)snap * ((size_t)L * L / 32);
+        const uint32_t y = (y0 + L - 1 + p / kS) % L, x = (x0 + L - 1 + p % kS) % L;
+        win[i] = packed_spin(base, L, x, y);
+    }
+}
+
+// Patch windows of every lattice of a handle for one round, and their keys.
+__global__ void gather_patches_kernel(DevState st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
+                                      uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nwin * kNPos; i += gridDim.x * blockDim.x) {
+        const int w = i / kNPos, p = i % kNPos;
+        int lo = 0, hi = n_lat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int)ll[mid].patch_begin <= w) lo = mid; else hi = mid - 1;
+        }
+        const LearnedLat d = ll[lo];
+        const uint32_t L = d.L, per_row = L / 16, j = (uint32_t)w - d.patch_begin;
+        const uint32_t a = j % per_row, b = j / per_row;
+        const uint32_t x0 = (16u * a + ox) % L, y0 = (16u * b + oy) % L;
+        const uint32_t y = (y0 + L - 1 + p / kS) % L, x = (x0 + L - 1 + p % kS) % L;
+        const int8_t s = packed_spin(st.spins + d.word_off, L, x, y);
+        win[i] = s;
+        win2[i] = s;
+        if (p == 0) keys[w] = LearnedKey{d.key0, d.key1, d.sim, j};
+    }
+}
+
+// Energy of the bonds touching the interior of a window.
+__device__ int local_energy(const int8_t* w) {
+    int e = 0;
+    for (int r = 1; r <= kP; ++r)
+        for (int c = 0; c < kS - 1; ++c) e -= w[r * kS + c] * w[r * kS + c + 1];
+    for (int c = 1; c <= kP; ++c)
+        for (int r = 0; r < kS - 1; ++r) e -= w[r * kS + c] * w[(r + 1) * kS + c];
+    return e;
+}
+
+// Metropolis-Hastings acceptance (FP64) and write-back of accepted patches.
+__global__ void mh_apply_kernel(DevState st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox, uint32_t oy,
+                                const int8_t* win_old, const int8_t* win_new, const float* lq_old,
+                                const float* lq_new, uint32_t round_t, unsigned long long* accepted) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    int lo = 0, hi = n_lat - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)ll[mid].patch_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    const LearnedLat d = ll[lo];
+    const int8_t* xo = win_old + (size_t)w * kNPos;
+    const int8_t* xn = win_new + (size_t)w * kNPos;
+    const int dE = local_energy(xn) - local_energy(xo);
+    const double log_alpha = -(double)dE * d.beta + (double)lq_old[w] - (double)lq_new[w];
+    const uint32_t j = (uint32_t)w - d.patch_begin;
+    const uint4 r = philox(j, round_t, d.sim, 5u, d.key0, d.key1);
+    const double u = ((double)((r.x >> 5) * 67108864ull + (r.y >> 6)) + 0.5) / 9007199254740992.0;
+    if (!(log(u) < log_alpha)) return;
+    const uint32_t L = d.L, wn = L >> 6, per_row = L / 16, a = j % per_row, b = j / per_row;
+    const uint32_t x0 = (16u * a + ox) % L, y0 = (16u * b + oy) % L;
+    int dM = 0;
+    for (int rr = 0; rr < kP; ++rr) {
+        const uint32_t y = (y0 + rr) % L;
+        uint32_t mask[2] = {0u, 0u};
+        uint32_t widx[2] = {0u, 0u};
+        for (int cc = 0; cc < kP; ++cc) {
+            const int8_t so = xo[(rr + 1) * kS + cc + 1], sn = xn[(rr + 1) * kS + cc + 1];
+            dM += sn - so;
+            const uint32_t x = (x0 + cc) % L, c = (x + y) & 1u, jj = x >> 1;
+            widx[c] = ((uint32_t)c * L + y) * wn + (jj >> 5);
+            if (so != sn) mask[c] |= 1u << (jj & 31);
+        }
+        for (int c = 0; c < 2; ++c)
+            if (mask[c]) atomicXor(&st.spins[d.word_off + widx[c]], mask[c]);
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat]), (unsigned long long)(long long)dE);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat + 1]), (unsigned long long)(long long)dM);
+    atomicAdd(&accepted[d.lat], 1ull);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launch wrappers (used by the C ABI below)
+// ---------------------------------------------------------------------------
+static int fwd_blocks(int n) { return (n + 16 * kWarpsFwd - 1) / (16 * kWarpsFwd); }
+
+cudaError_t configure_learned_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(ar_net_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kWarpsFwd * kWarpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ar_net_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpsFwd * kWarpSmem);
+    const int bwd = (((kNParams + 3) / 4) * 4 + kWarpsBwd * 2 * kNPos * kC) * (int)sizeof(float);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(net_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd);
+    return e;
+}
+
+cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z, __nv_bfloat16* h,
+                               cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    NetPtrs np{ns.wb, ns.w};
+    ar_net_kernel<0><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(
+        np, const_cast<int8_t*>(win), n, lq, z, h, nullptr, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
+                              uint32_t round_t, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    NetPtrs np{ns.wb, ns.w};
+    ar_net_kernel<1><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(np, win, n, lq, nullptr,
+                                                                                     nullptr, keys, round_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, const float* z,
+                                const __nv_bfloat16* h, float* grad, float* loss, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    NetPtrs np{ns.wb, ns.w};
+    const int bwd = (((kNParams + 3) / 4) * 4 + kWarpsBwd * 2 * kNPos * kC) * (int)sizeof(float);
+    int blocks = (n + kWarpsBwd - 1) / kWarpsBwd;
+    blocks = std::min(blocks, device_sm_count() * 2);
+    net_backward_kernel<<<blocks, kWarpsBwd * 32, bwd, stream>>>(np, win, n, z, h, grad, loss, 1.0f / (float)n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream) {
+    const float bc1 = 1.0f - powf(0.9f, (float)step), bc2 = 1.0f - powf(0.999f, (float)step);
+    adam_kernel<<<(kNParams + 255) / 256, 256, 0, stream>>>(ns.w, ns.m, ns.v, ns.g, ns.wb, lr, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const NetState& ns, cudaStream_t stream) {
+    to_bf16_kernel<<<(kNParams + 255) / 256, 256, 0, stream>>>(ns.w, ns.wb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_windows(const uint32_t* pool, int n_snap, uint32_t L, int nwin, uint64_t seed,
+                                 uint32_t step, int8_t* win, cudaStream_t stream) {
+    const int blocks = std::min((nwin * kNPos + 255) / 256, device_sm_count() * 8);
+    train_windows_kernel<<<blocks, 256, 0, stream>>>(pool, n_snap, L, nwin, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                    step, win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_patches(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
+                                  uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys, cudaStream_t stream) {
+    if (nwin <= 0) return cudaSuccess;
+    const int blocks = std::min((nwin * kNPos + 255) / 256, device_sm_count() * 8);
+    gather_patches_kernel<<<blocks, 256, 0, stream>>>(st, ll, n_lat, nwin, ox, oy, win, win2, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mh_apply(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox, uint32_t oy,
+                            const int8_t* win_old, const int8_t* win_new, const float* lq_old, const float* lq_new,
+                            uint32_t round_t, unsigned long long* accepted, cudaStream_t stream) {
+    if (nwin <= 0) return cudaSuccess;
+    mh_apply_kernel<<<(nwin + 127) / 128, 128, 0, stream>>>(st, ll, n_lat, nwin, ox, oy, win_old, win_new, lq_old,
+                                                           lq_new, round_t, accepted);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

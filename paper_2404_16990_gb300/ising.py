@@ -92,6 +92,21 @@ def _load():
             "ising_destroy": ([vp], None),
             "ising_sweep_noalloc": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_uint64), i64, i64, vp, vp], ctypes.c_int),
+            "ising_net_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_net_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, sz, vp], ctypes.c_int),
+            "ising_net_destroy": ([vp], None),
+            "ising_net_set_params": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_net_get_params": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_net_score": ([vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_net_sample": ([vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.c_uint32, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_net_grad": ([vp, ctypes.POINTER(ctypes.c_int8), ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_net_train": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_float,
+                                 ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ising_learned_round": ([vp, vp, i64, i64p], ctypes.c_int),
+            "ising_snapshot": ([vp, vp, sz], ctypes.c_int),
             "ising_binder": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -326,6 +341,89 @@ def ising_tau_int(x, c: float = 6.0):
     return tau.value, err.value, w.value
 
 
+ISING_NET_PARAMS = 2945
+
+
+class IsingNet:
+    """Owner of a learned-proposal network handle and its torch-allocated
+    device workspace (ising_net_* in ising.h)."""
+
+    def __init__(self, max_windows: int, max_lattices: int = 1, stream=None, device=None):
+        import torch
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        lib = _load()
+        nb = ctypes.c_size_t(0)
+        _check(lib.ising_net_workspace_bytes(max_windows, max_lattices, ctypes.byref(nb)))
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        self.h = ctypes.c_void_p()
+        _check(lib.ising_net_create(ctypes.byref(self.h), max_windows, max_lattices, self.workspace.data_ptr(),
+                                    nb.value, self.stream.cuda_stream))
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == ISING_NET_PARAMS
+        _check(_load().ising_net_set_params(self.h, _ptr(p, ctypes.c_float)))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(ISING_NET_PARAMS, dtype=np.float32)
+        _check(_load().ising_net_get_params(self.h, _ptr(p, ctypes.c_float)))
+        return p
+
+    def score(self, windows, with_z: bool = False):
+        w = np.ascontiguousarray(windows, dtype=np.int8).reshape(-1, 100)
+        lq = np.zeros(len(w), dtype=np.float32)
+        z = np.zeros((len(w), 100), dtype=np.float32) if with_z else None
+        _check(_load().ising_net_score(self.h, _ptr(w, ctypes.c_int8), len(w), _ptr(lq, ctypes.c_float),
+                                       _ptr(z, ctypes.c_float) if with_z else None))
+        return (lq, z) if with_z else lq
+
+    def sample(self, windows, keys, round_index: int):
+        w = np.array(windows, dtype=np.int8).reshape(-1, 100)
+        k = np.ascontiguousarray(keys, dtype=np.uint32).reshape(-1, 4)
+        lq = np.zeros(len(w), dtype=np.float32)
+        _check(_load().ising_net_sample(self.h, _ptr(w, ctypes.c_int8), len(w), _ptr(k, ctypes.c_uint32),
+                                        round_index, _ptr(lq, ctypes.c_float)))
+        return w, lq
+
+    def grad(self, windows):
+        w = np.ascontiguousarray(windows, dtype=np.int8).reshape(-1, 100)
+        g = np.zeros(ISING_NET_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        _check(_load().ising_net_grad(self.h, _ptr(w, ctypes.c_int8), len(w), _ptr(g, ctypes.c_float),
+                                      ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, dev_pool_words: int, n_snap: int, L: int, steps: int, batch: int, lr: float, seed: int):
+        losses = np.zeros(max(1, steps), dtype=np.float32)
+        _check(_load().ising_net_train(self.h, dev_pool_words, n_snap, L, steps, batch, lr, seed,
+                                       _ptr(losses, ctypes.c_float)))
+        return losses[:steps]
+
+    def close(self):
+        if getattr(self, "h", None):
+            _load().ising_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ising_snapshot(h, dev_dst: int, nbytes: int) -> None:
+    _check(_load().ising_snapshot(h, dev_dst, nbytes))
+
+
+def ising_learned_round(h, net: "IsingNet", round_index: int) -> np.ndarray:
+    n = ising_num_sims(h)
+    acc = np.zeros(max(1, n), dtype=np.int64)
+    _check(_load().ising_learned_round(h, net.h, round_index, _ptr(acc, ctypes.c_int64)))
+    return acc[:n]
+
+
 class IsingSim:
     """Owner of one handle and its torch-allocated device workspace.
 
@@ -383,6 +481,9 @@ class IsingSim:
 
     def set_plan(self, plan: int, **kw) -> None:
         ising_set_plan(self.h, plan, **kw)
+
+    def learned_round(self, net: "IsingNet", round_index: int) -> np.ndarray:
+        return ising_learned_round(self.h, net, round_index)
 
     def autotune(self, probe_sweeps: int = 10, force: bool = False) -> float:
         return ising_autotune(self.h, probe_sweeps, force)
