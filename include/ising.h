@@ -299,10 +299,18 @@ int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int
                     int batch, float lr, uint64_t seed, float* host_losses);
 
 /* One learned patch round over every lattice of h (round index round_index;
- * L must be a multiple of 16, which every valid L is).  Accepted patches per
- * lattice go to host_accepted [n_sims] if not NULL.  The handle's sweep
- * counter is unchanged; its current E and M are updated. */
+ * L must be a multiple of 16, which every valid L is), on h's stream.  With
+ * host_accepted [n_sims] not NULL the call synchronises and returns the
+ * patches accepted in this round; with NULL it only enqueues the round and the
+ * per-lattice counts accumulate on the device (read them with
+ * ising_net_accepted).  The first round with a handle uploads its lattice
+ * table (synchronising once).  The handle's sweep counter is unchanged; its
+ * current E and M are updated exactly. */
 int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t* host_accepted);
+
+/* Accepted patches per lattice accumulated by rounds enqueued without a host
+ * buffer (host [n]); reset = 1 zeroes the counters.  Synchronises the device. */
+int ising_net_accepted(ising_net_t net, int64_t* host_accepted, int n, int reset);
 
 /* Allocation-free streaming sweep.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code running

@@ -933,6 +933,9 @@ struct ising_net {
     LearnedLat* ll = nullptr;
     unsigned long long* accepted = nullptr;
     int step = 0;
+    const ising_handle* table_owner = nullptr;   // handle whose lattice table is on the device
+    std::vector<LearnedLat> table;
+    int table_windows = 0;
 };
 
 namespace {
@@ -1117,34 +1120,44 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
     if (round_index < 0 || round_index > (int64_t)0xFFFFFFFFll) return fail(ISING_EINVAL, "round_index out of range");
     if (h->n == 0) return ISING_OK;
     if (h->n > net->max_lattices) return fail(ISING_EINVAL, "handle has %d lattices, net allows %d", h->n, net->max_lattices);
-    std::vector<LearnedLat> ll(h->n);
-    int64_t nwin = 0;
-    for (int i = 0; i < h->n; ++i) {
-        LearnedLat d{};
-        d.word_off = h->layout.word_off[i];
-        d.L = (uint32_t)h->L[i];
-        d.lat = (uint32_t)i;
-        d.sim = (uint32_t)i;
-        d.key0 = (uint32_t)(h->seed[i] & 0xFFFFFFFFull);
-        d.key1 = (uint32_t)(h->seed[i] >> 32);
-        d.patch_begin = (uint32_t)nwin;
-        d.beta = 1.0 / h->T[i];
-        ll[i] = d;
-        nwin += (int64_t)(h->L[i] / 16) * (h->L[i] / 16);
+    // the lattice table depends only on the handle: upload it when the handle
+    // changes, from a host copy that lives as long as the net
+    if (net->table_owner != h) {
+        net->table.assign(h->n, LearnedLat{});
+        int64_t nwin = 0;
+        for (int i = 0; i < h->n; ++i) {
+            LearnedLat d{};
+            d.word_off = h->layout.word_off[i];
+            d.L = (uint32_t)h->L[i];
+            d.lat = (uint32_t)i;
+            d.sim = (uint32_t)i;
+            d.key0 = (uint32_t)(h->seed[i] & 0xFFFFFFFFull);
+            d.key1 = (uint32_t)(h->seed[i] >> 32);
+            d.patch_begin = (uint32_t)nwin;
+            d.beta = 1.0 / h->T[i];
+            net->table[i] = d;
+            nwin += (int64_t)(h->L[i] / 16) * (h->L[i] / 16);
+        }
+        if (nwin > net->max_windows)
+            return fail(ISING_EINVAL, "round needs %lld windows, net allows %d", (long long)nwin, net->max_windows);
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+        CUDA_TRY(cudaMemcpy(net->ll, net->table.data(), net->table.size() * sizeof(LearnedLat), cudaMemcpyHostToDevice),
+                 "upload lattice table");
+        CUDA_TRY(cudaMemset(net->accepted, 0, (size_t)net->max_lattices * 8), "zero counters");
+        net->table_owner = h;
+        net->table_windows = (int)nwin;
     }
-    if (nwin > net->max_windows) return fail(ISING_EINVAL, "round needs %lld windows, net allows %d",
-                                             (long long)nwin, net->max_windows);
     static const uint32_t off[4][2] = {{0, 0}, {8, 8}, {0, 8}, {8, 0}};
     const uint32_t ox = off[round_index % 4][0], oy = off[round_index % 4][1];
     const uint32_t rt = (uint32_t)round_index;
-    CUDA_TRY(cudaMemcpyAsync(net->ll, ll.data(), ll.size() * sizeof(LearnedLat), cudaMemcpyHostToDevice, h->stream),
-             "upload lattice table");
-    CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
-    CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, (int)nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
+    const int nwin = net->table_windows;
+    if (host_accepted)
+        CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
+    CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
              "gather patches");
-    CUDA_TRY(launch_net_forward(net->ns, net->win, (int)nwin, net->lq, nullptr, nullptr, h->stream), "score");
-    CUDA_TRY(launch_net_sample(net->ns, net->win2, (int)nwin, net->lq2, net->keys, rt, h->stream), "sample");
-    CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, (int)nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
+    CUDA_TRY(launch_net_forward(net->ns, net->win, nwin, net->lq, nullptr, nullptr, h->stream), "score");
+    CUDA_TRY(launch_net_sample(net->ns, net->win2, nwin, net->lq2, net->keys, rt, h->stream), "sample");
+    CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
                              net->accepted, h->stream), "accept");
     if (host_accepted) {
         std::vector<unsigned long long> acc(h->n);
@@ -1152,9 +1165,19 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
                  "copy counters");
         CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
         for (int i = 0; i < h->n; ++i) host_accepted[i] = (int64_t)acc[i];
-    } else {
-        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");   // the lattice table is a host buffer
+        CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
     }
+    return ISING_OK;
+}
+
+int ising_net_accepted(ising_net_t net, int64_t* host_accepted, int n, int reset) {
+    if (!net || !host_accepted || n < 0 || n > net->max_lattices) return fail(ISING_EINVAL, "invalid arguments");
+    std::vector<unsigned long long> acc((size_t)std::max(n, 1));
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+    CUDA_TRY(cudaMemcpy(acc.data(), net->accepted, (size_t)n * 8, cudaMemcpyDeviceToHost), "copy counters");
+    for (int i = 0; i < n; ++i) host_accepted[i] = (int64_t)acc[i];
+    if (reset) CUDA_TRY(cudaMemset(net->accepted, 0, (size_t)net->max_lattices * 8), "zero counters");
     return ISING_OK;
 }
 

@@ -10,7 +10,53 @@
 #include "ising_internal.h"
 
 #include <cmath>
+#include <complex>
 #include <cstdint>
+#include <vector>
+
+namespace {
+
+// In-place iterative radix-2 FFT (Cooley-Tukey); n is a power of two.
+void fft(std::vector<std::complex<double>>& a, bool inverse) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = 2.0 * M_PI / (double)len * (inverse ? 1.0 : -1.0);
+        const std::complex<double> wl(std::cos(ang), std::sin(ang));
+        for (size_t i = 0; i < n; i += len) {
+            std::complex<double> w(1.0, 0.0);
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+                w *= wl;
+            }
+        }
+    }
+    if (inverse)
+        for (auto& x : a) x /= (double)n;
+}
+
+// sum_{i} d[i] d[i + lag] for lag = 0 .. n-1 (d = x - mean), by FFT.
+std::vector<double> autocov_sums(const double* x, int64_t n, double mean) {
+    size_t m = 1;
+    while (m < 2 * (size_t)n) m <<= 1;
+    std::vector<std::complex<double>> a(m, 0.0);
+    for (int64_t i = 0; i < n; ++i) a[i] = x[i] - mean;
+    fft(a, false);
+    for (auto& v : a) v = std::complex<double>(std::norm(v), 0.0);
+    fft(a, true);
+    std::vector<double> out((size_t)n);
+    for (int64_t i = 0; i < n; ++i) out[i] = a[i].real();
+    return out;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -33,9 +79,17 @@ int ising_tau_int(const double* x, int64_t n, double c, double* tau, double* tau
     double t = 0.5;
     int64_t M = 0;
     const int64_t max_lag = n / 2;
+    // autocovariance sums for every lag at once (FFT) on long series, one lag
+    // at a time on short ones
+    std::vector<double> sums;
+    if (n >= 4096) sums = autocov_sums(x, n, mean);
     for (int64_t lag = 1; lag <= max_lag; ++lag) {
         double s = 0.0;
-        for (int64_t i = 0; i + lag < n; ++i) s += (x[i] - mean) * (x[i + lag] - mean);
+        if (!sums.empty()) {
+            s = sums[(size_t)lag];
+        } else {
+            for (int64_t i = 0; i + lag < n; ++i) s += (x[i] - mean) * (x[i + lag] - mean);
+        }
         const double rho = s / ((double)n * c0);
         t += rho;
         M = lag;

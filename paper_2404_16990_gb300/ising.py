@@ -107,6 +107,7 @@ def _load():
                                  ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ising_learned_round": ([vp, vp, i64, i64p], ctypes.c_int),
             "ising_snapshot": ([vp, vp, sz], ctypes.c_int),
+            "ising_net_accepted": ([vp, i64p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "ising_binder": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -401,6 +402,11 @@ class IsingNet:
                                        _ptr(losses, ctypes.c_float)))
         return losses[:steps]
 
+    def accepted(self, n: int, reset: bool = True) -> np.ndarray:
+        acc = np.zeros(max(1, n), dtype=np.int64)
+        _check(_load().ising_net_accepted(self.h, _ptr(acc, ctypes.c_int64), n, 1 if reset else 0))
+        return acc[:n]
+
     def close(self):
         if getattr(self, "h", None):
             _load().ising_net_destroy(self.h)
@@ -417,8 +423,13 @@ def ising_snapshot(h, dev_dst: int, nbytes: int) -> None:
     _check(_load().ising_snapshot(h, dev_dst, nbytes))
 
 
-def ising_learned_round(h, net: "IsingNet", round_index: int) -> np.ndarray:
+def ising_learned_round(h, net: "IsingNet", round_index: int, sync: bool = True):
+    """One learned round; returns the accepted patches per lattice when sync,
+    else enqueues only (counts accumulate; see IsingNet.accepted)."""
     n = ising_num_sims(h)
+    if not sync:
+        _check(_load().ising_learned_round(h, net.h, round_index, None))
+        return None
     acc = np.zeros(max(1, n), dtype=np.int64)
     _check(_load().ising_learned_round(h, net.h, round_index, _ptr(acc, ctypes.c_int64)))
     return acc[:n]
@@ -482,8 +493,8 @@ class IsingSim:
     def set_plan(self, plan: int, **kw) -> None:
         ising_set_plan(self.h, plan, **kw)
 
-    def learned_round(self, net: "IsingNet", round_index: int) -> np.ndarray:
-        return ising_learned_round(self.h, net, round_index)
+    def learned_round(self, net: "IsingNet", round_index: int, sync: bool = True):
+        return ising_learned_round(self.h, net, round_index, sync)
 
     def autotune(self, probe_sweeps: int = 10, force: bool = False) -> float:
         return ising_autotune(self.h, probe_sweeps, force)

@@ -159,3 +159,22 @@ def test_training_lowers_the_loss():
     z0, _ = ol.forward(win, ol.init_params(1, gain=0.5))
     z1, _ = ol.forward(win, p_trained.astype(np.float64))
     assert ol.log_q(win, z1).mean() > ol.log_q(win, z0).mean()
+
+
+def test_async_rounds_match_synchronous_rounds():
+    flat = ol.init_params(23, gain=0.3)
+    a = ising.IsingSim(128, [3.0, 3.3], 8)
+    b = ising.IsingSim(128, [3.0, 3.3], 8)
+    na = ising.IsingNet(max_windows=128, max_lattices=2)
+    nb = ising.IsingNet(max_windows=128, max_lattices=2)
+    na.set_params(flat)
+    nb.set_params(flat)
+    tot = np.zeros(2, np.int64)
+    for r in range(6):
+        tot += a.learned_round(na, r)
+        a.sweep(1)
+        b.learned_round(nb, r, sync=False)
+        b.sweep(1)
+    assert np.array_equal(nb.accepted(2), tot) and tot.sum() > 0
+    for i in range(2):
+        assert np.array_equal(a.spins(i), b.spins(i))

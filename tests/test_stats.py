@@ -49,8 +49,8 @@ def test_binder_limits():
 
 
 def test_library_tau_int_matches_oracle():
-    for rho, seed in [(0.0, 3), (0.6, 4), (0.95, 5)]:
-        x = ar1(rho, 50_000, seed)
+    for rho, seed, n in [(0.0, 3, 50_000), (0.6, 4, 50_000), (0.95, 5, 50_000), (0.9, 6, 3000), (0.99, 7, 200_000)]:
+        x = ar1(rho, n, seed)
         lib = ising.ising_tau_int(x, 6.0)
         ref = ostats.tau_int(x, 6.0)
         assert lib[2] == ref[2]
