@@ -269,6 +269,18 @@ int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* 
                      size_t ws_bytes, void* cuda_stream);
 void ising_net_destroy(ising_net_t net);
 
+/* Arithmetic of scoring, sampling and rounds (training is always BF16):
+ * ISING_NET_BF16 as above, or ISING_NET_FP8: weights enter as
+ * e4m3(W * s_l) with s_l = 2^floor(log2(448 / max|W of layer l|)) (layers 1..4),
+ * hidden activations as e4m3(relu(.)) (round to nearest even, saturating),
+ * products summed in fp32 (mma.sync e4m3, K = 32: taps 0+1, 2+3, 4) and
+ * divided by s_l before the fp32 bias.  The MH correction uses the same
+ * arithmetic for x and x', so either precision samples the Boltzmann
+ * distribution exactly; FP8 changes only the acceptance rate and the cost. */
+#define ISING_NET_BF16 0
+#define ISING_NET_FP8 1
+int ising_net_set_precision(ising_net_t net, int precision);
+
 /* fp32 parameters in/out (host, ISING_NET_PARAMS); set also zeroes the Adam
  * moments and its step count. */
 int ising_net_set_params(ising_net_t net, const float* host_params);

@@ -56,6 +56,33 @@ def bf16(a):
     return r.view(np.float32).astype(np.float64)
 
 
+def e4m3(a):
+    """Round to float8 E4M3 (1-4-3, bias 7, largest finite 448; round to
+    nearest even, saturating), back to float64."""
+    a = np.asarray(a, dtype=np.float64)
+    sgn = np.sign(a)
+    x = np.minimum(np.abs(a), 448.0)
+    e = np.floor(np.log2(np.maximum(x, 2.0 ** -10)))
+    e = np.maximum(e, -6.0)                       # subnormals: step 2^-9
+    step = 2.0 ** (e - 3.0)
+    q = np.minimum(np.round(x / step) * step, 448.0)   # np.round: half to even
+    return sgn * q
+
+
+LAYER_W = {"W1": 0, "W2": 1, "W3": 2, "W4": 3}
+
+
+def fp8_scales(flat):
+    """Per-layer power-of-two weight scales: 2^floor(log2(448 / max|W|))."""
+    P = unpack(flat)
+    out = []
+    for k in ("W1", "W2", "W3", "W4"):
+        mx = float(np.max(np.abs(np.asarray(P[k], np.float32).astype(np.float64))))
+        e = math.floor(math.log2(448.0 / mx)) if mx > 0 else 0
+        out.append(2.0 ** min(max(e, -60), 60))
+    return out
+
+
 def unpack(flat):
     flat = np.asarray(flat, dtype=np.float64)
     assert flat.size == N_PARAMS
@@ -121,11 +148,19 @@ def features(win):
     return F
 
 
-def forward(win, flat, exact=False):
-    """Teacher-forced pass.  Returns (z [B, S, S], cache)."""
+def forward(win, flat, exact=False, prec="bf16"):
+    """Teacher-forced pass.  Returns (z [B, S, S], cache).  prec = "bf16"
+    (weights and hidden activations rounded to bf16) or "fp8" (weights as
+    e4m3(W s_l) / s_l, hidden activations as e4m3)."""
     P = unpack(flat)
-    q = (lambda a: a) if exact else bf16
-    W = {k: q(v) if k.startswith("W") else v for k, v in P.items()}
+    if prec == "fp8" and not exact:
+        sc = fp8_scales(flat)
+        q = e4m3
+        W = {k: (e4m3(np.asarray(v, np.float32).astype(np.float64) * sc[LAYER_W[k]]) / sc[LAYER_W[k]]
+                 if k.startswith("W") else v) for k, v in P.items()}
+    else:
+        q = (lambda a: a) if exact else bf16
+        W = {k: q(v) if k.startswith("W") else v for k, v in P.items()}
     F = features(win)
     A1 = F @ W["W1"] + P["b1"]
     H1 = q(np.maximum(A1, 0.0))
@@ -262,7 +297,7 @@ def sample_threshold(z):
     return np.where(s32 >= np.float32(1.0), 4294967295.0, t)
 
 
-def sample(win_ring, flat, R):
+def sample(win_ring, flat, R, prec="bf16"):
     """Autoregressive sample of the interior given the ring.  win_ring:
     [B, S, S] (interior values ignored), R [B, P*P] raw u32 draws in raster
     order.  x'_p = +1 iff R_p < floor(2^32 sigmoid(z_p)).  Returns (windows,
@@ -274,10 +309,10 @@ def sample(win_ring, flat, R):
     thr = np.zeros((B, P * P))
     for i in range(P * P):
         r, c = 1 + i // P, 1 + i % P
-        z, _ = forward(w, flat)
+        z, _ = forward(w, flat, prec=prec)
         thr[:, i] = sample_threshold(z[:, r, c])
         w[:, r, c] = np.where(np.asarray(R[:, i], np.float64) < thr[:, i], 1.0, -1.0)
-    z, _ = forward(w, flat)
+    z, _ = forward(w, flat, prec=prec)
     return w.astype(np.int8), log_q(w, z), thr
 
 
@@ -288,7 +323,7 @@ def sampling_draws(seed, s, j, round_index, P=8):
     return np.array([oracle.site_random(seed, 64 * j + i, round_index, s, 4) for i in range(P * P)], np.float64)
 
 
-def learned_round(sigma, flat, T, seed, s, round_index, P=8):
+def learned_round(sigma, flat, T, seed, s, round_index, P=8, prec="bf16"):
     """One MH patch round on lattice sigma (in place).  Uniforms: Philox
     phase 4 (sampling: counter (16 j + i/4, round, s, 4), lane i % 4) and phase
     5 (acceptance: counter (j, round, s, 5), lanes 0, 1).  Returns
@@ -297,10 +332,10 @@ def learned_round(sigma, flat, T, seed, s, round_index, P=8):
     L = sigma.shape[0]
     origins = patch_origins(L, round_index, P)
     wins = np.stack([extract(sigma, x0, y0, P) for (x0, y0) in origins])
-    z, _ = forward(wins, flat)
+    z, _ = forward(wins, flat, prec=prec)
     lq_old = log_q(wins, z)
     R = np.stack([sampling_draws(seed, s, j, round_index, P) for j in range(len(origins))])
-    new, lq_new, thr = sample(wins, flat, R)
+    new, lq_new, thr = sample(wins, flat, R, prec=prec)
     dE = local_energy(new) - local_energy(wins)
     acc = 0
     dEt = dMt = 0

@@ -933,6 +933,8 @@ struct ising_net {
     LearnedLat* ll = nullptr;
     unsigned long long* accepted = nullptr;
     int step = 0;
+    int precision = ISING_NET_BF16;
+    bool fp8_stale = true;                        // masters changed since the e4m3 copy was made
     const ising_handle* table_owner = nullptr;   // handle whose lattice table is on the device
     std::vector<LearnedLat> table;
     int table_windows = 0;
@@ -941,7 +943,7 @@ struct ising_net {
 namespace {
 
 struct NetLayout {
-    size_t w, m, v, g, wb, loss, win, win2, z, lq, lq2, h, keys, ll, acc, total;
+    size_t w, m, v, g, wb, loss, wq, wscale, win, win2, z, lq, lq2, h, keys, ll, acc, total;
 };
 
 NetLayout net_layout(int W, int NL) {
@@ -951,6 +953,8 @@ NetLayout net_layout(int W, int NL) {
     const size_t P = ISING_NET_PARAMS, w = (size_t)W;
     l.w = take(P * 4); l.m = take(P * 4); l.v = take(P * 4); l.g = take(P * 4); l.wb = take(P * 2);
     l.loss = take(16);
+    l.wq = take(P);
+    l.wscale = take(16);
     l.win = take(w * 100); l.win2 = take(w * 100);
     l.z = take(w * 100 * 4);
     l.lq = take(w * 4); l.lq2 = take(w * 4);
@@ -971,9 +975,51 @@ int net_upload_windows(ising_net* net, const int8_t* host, int n) {
     return ISING_OK;
 }
 
+// Per-layer power-of-two scales of the e4m3 weight copy: the largest |W| of a
+// layer times its scale is at most 448 (the largest finite e4m3 value).
+int net_refresh_fp8(ising_net* net) {
+    if (!net->fp8_stale) return ISING_OK;
+    std::vector<float> w(ISING_NET_PARAMS);
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    CUDA_TRY(cudaMemcpy(w.data(), net->ns.w, w.size() * sizeof(float), cudaMemcpyDeviceToHost), "read params");
+    const int lo[4] = {0, 272, 1568, 2864}, hi[4] = {256, 1552, 2848, 2944};
+    float scale[4];
+    for (int l = 0; l < 4; ++l) {
+        double mx = 0.0;
+        for (int i = lo[l]; i < hi[l]; ++i) mx = std::max(mx, (double)std::fabs(w[i]));
+        double e = mx > 0.0 ? std::floor(std::log2(448.0 / mx)) : 0.0;
+        e = std::min(std::max(e, -60.0), 60.0);
+        scale[l] = (float)std::ldexp(1.0, (int)e);
+    }
+    CUDA_TRY(cudaMemcpy(net->ns.wscale, scale, sizeof(scale), cudaMemcpyHostToDevice), "upload scales");
+    CUDA_TRY(launch_to_fp8(net->ns, net->stream), "e4m3 copy");
+    CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    net->fp8_stale = false;
+    return ISING_OK;
+}
+
+cudaError_t net_score(ising_net* net, const int8_t* win, int n, float* lq, float* z, cudaStream_t st) {
+    if (net->precision == ISING_NET_FP8) return launch_net_forward_fp8(net->ns, win, n, lq, z, st);
+    return launch_net_forward(net->ns, win, n, lq, z, nullptr, st);
+}
+
+cudaError_t net_sample(ising_net* net, int8_t* win, int n, float* lq, uint32_t round_t, cudaStream_t st) {
+    if (net->precision == ISING_NET_FP8) return launch_net_sample_fp8(net->ns, win, n, lq, net->keys, round_t, st);
+    return launch_net_sample(net->ns, win, n, lq, net->keys, round_t, st);
+}
+
 }  // namespace
 
 extern "C" {
+
+int ising_net_set_precision(ising_net_t net, int precision) {
+    if (!net) return fail(ISING_EINVAL, "net is NULL");
+    if (precision != ISING_NET_BF16 && precision != ISING_NET_FP8)
+        return fail(ISING_EINVAL, "precision must be ISING_NET_BF16 or ISING_NET_FP8");
+    net->precision = precision;
+    if (precision == ISING_NET_FP8) return net_refresh_fp8(net);
+    return ISING_OK;
+}
 
 int ising_net_workspace_bytes(int max_windows, int max_lattices, size_t* bytes) {
     if (!bytes || max_windows < 1 || max_lattices < 1)
@@ -998,7 +1044,8 @@ int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* 
     net->stream = (cudaStream_t)cuda_stream;
     net->ws = b;
     net->ns = NetState{(float*)(b + l.w), (float*)(b + l.m), (float*)(b + l.v), (float*)(b + l.g),
-                       (__nv_bfloat16*)(b + l.wb), (float*)(b + l.loss)};
+                       (__nv_bfloat16*)(b + l.wb), (float*)(b + l.loss), (uint8_t*)(b + l.wq),
+                       (float*)(b + l.wscale)};
     net->win = (int8_t*)(b + l.win);
     net->win2 = (int8_t*)(b + l.win2);
     net->z = (float*)(b + l.z);
@@ -1032,6 +1079,8 @@ int ising_net_set_params(ising_net_t net, const float* host) {
     CUDA_TRY(launch_to_bf16(net->ns, net->stream), "bf16 copy");
     CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
     net->step = 0;
+    net->fp8_stale = true;
+    if (net->precision == ISING_NET_FP8) return net_refresh_fp8(net);
     return ISING_OK;
 }
 
@@ -1047,8 +1096,7 @@ int ising_net_score(ising_net_t net, const int8_t* host_windows, int n, float* h
     if (!net || !host_logq) return fail(ISING_EINVAL, "NULL argument");
     int rc = net_upload_windows(net, host_windows, n);
     if (rc != ISING_OK) return rc;
-    CUDA_TRY(launch_net_forward(net->ns, net->win, n, net->lq, host_z ? net->z : nullptr, nullptr, net->stream),
-             "score");
+    CUDA_TRY(net_score(net, net->win, n, net->lq, host_z ? net->z : nullptr, net->stream), "score");
     CUDA_TRY(cudaMemcpyAsync(host_logq, net->lq, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream), "copy logq");
     if (host_z)
         CUDA_TRY(cudaMemcpyAsync(host_z, net->z, (size_t)n * 400, cudaMemcpyDeviceToHost, net->stream), "copy z");
@@ -1063,7 +1111,7 @@ int ising_net_sample(ising_net_t net, int8_t* host_windows, int n, const uint32_
     if (rc != ISING_OK) return rc;
     CUDA_TRY(cudaMemcpyAsync(net->keys, host_keys, (size_t)n * sizeof(LearnedKey), cudaMemcpyHostToDevice,
                              net->stream), "upload keys");
-    CUDA_TRY(launch_net_sample(net->ns, net->win, n, net->lq, net->keys, round_index, net->stream), "sample");
+    CUDA_TRY(net_sample(net, net->win, n, net->lq, round_index, net->stream), "sample");
     CUDA_TRY(cudaMemcpyAsync(host_windows, net->win, (size_t)n * 100, cudaMemcpyDeviceToHost, net->stream),
              "copy windows");
     CUDA_TRY(cudaMemcpyAsync(host_logq, net->lq, (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream), "copy logq");
@@ -1112,6 +1160,8 @@ int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int
                                      net->stream), "copy loss");
     }
     CUDA_TRY(cudaStreamSynchronize(net->stream), "synchronize");
+    net->fp8_stale = true;
+    if (net->precision == ISING_NET_FP8 && steps > 0) return net_refresh_fp8(net);
     return ISING_OK;
 }
 
@@ -1155,8 +1205,8 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
         CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
     CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
              "gather patches");
-    CUDA_TRY(launch_net_forward(net->ns, net->win, nwin, net->lq, nullptr, nullptr, h->stream), "score");
-    CUDA_TRY(launch_net_sample(net->ns, net->win2, nwin, net->lq2, net->keys, rt, h->stream), "sample");
+    CUDA_TRY(net_score(net, net->win, nwin, net->lq, nullptr, h->stream), "score");
+    CUDA_TRY(net_sample(net, net->win2, nwin, net->lq2, rt, h->stream), "sample");
     CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
                              net->accepted, h->stream), "accept");
     if (host_accepted) {

@@ -86,6 +86,8 @@ struct NetState {
     float* g;              // gradient accumulator
     __nv_bfloat16* wb;     // bf16 copy used by the tensor-core kernels
     float* loss;           // scalar
+    uint8_t* wq;           // e4m3 copy of the weights, scaled per layer (FP8 inference)
+    float* wscale;         // [4] per-layer power-of-two weight scales of the e4m3 copy
 };
 
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
@@ -113,6 +115,11 @@ cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, co
                                 const __nv_bfloat16* h, float* grad, float* loss, cudaStream_t stream);
 cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream);
 cudaError_t launch_to_bf16(const NetState& ns, cudaStream_t stream);
+cudaError_t launch_to_fp8(const NetState& ns, cudaStream_t stream);
+cudaError_t launch_net_forward_fp8(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
+                                   cudaStream_t stream);
+cudaError_t launch_net_sample_fp8(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
+                                  uint32_t round_t, cudaStream_t stream);
 cudaError_t launch_train_windows(const uint32_t* pool, int n_snap, uint32_t L, int nwin, uint64_t seed,
                                  uint32_t step, int8_t* win, cudaStream_t stream);
 cudaError_t launch_gather_patches(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,

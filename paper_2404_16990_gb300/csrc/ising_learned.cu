@@ -10,9 +10,10 @@
 //
 // Tensor cores: every layer of the net is a masked 3x3 convolution, i.e. a
 // contraction over (tap, input channel).  The kernels run it as
-// mma.sync.m16n8k16 BF16 x BF16 -> FP32: the M dimension is 16 windows of one
-// warp, K = 16 input channels of one tap (a k-step per tap), N = 16 output
-// channels (two n-tiles).  Positions are visited in raster order, so each
+// mma.sync.m16n8k16 BF16 x BF16 -> FP32: the M dimension holds the windows of
+// one warp (8 of the 16 rows, for twice the warps in flight on this
+// latency-bound sequence), K = 16 input channels of one tap (a k-step per tap),
+// N = 16 output channels (two n-tiles).  Positions are visited in raster order, so each
 // window position's activations are computed once, from already final earlier
 // positions: sampling, scoring and the training forward are the same code.
 #include "../../include/ising.h"
@@ -20,6 +21,7 @@
 #include "ising_device.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,12 +41,15 @@ constexpr int kOffW1 = 0, kOffB1 = 256, kOffW2 = 272, kOffB2 = 1552, kOffW3 = 15
               kOffW4 = 2864, kOffB4 = 2944;
 constexpr int kNParams = ISING_NET_PARAMS;
 static_assert(kOffB4 + 1 == ISING_NET_PARAMS, "parameter layout");
-constexpr int kWarpsFwd = 4;
-// per-warp shared memory of the forward kernel: spins [16][100] int8, then the
-// activation ring [3 layers][12 slots][16 windows][16 channels] bf16
-constexpr int kSpinBytes = 16 * kNPos;                       // 1600
-constexpr int kRingBytes = 3 * kSlots * 16 * kC * 2;          // 18432
-constexpr int kWarpSmem = kSpinBytes + kRingBytes;            // 20032 (multiple of 16)
+constexpr int kWarpsFwd = 5;
+constexpr int kWin = 8;                                       // windows per warp (rows 0..7 of the m16 tile)
+constexpr int kRowH = 24;                                     // bf16 per activation row: 16 + 8 padding
+// per-warp shared memory of the forward kernel: spins [8][100] int8, then the
+// activation ring [3 layers][12 slots][8 windows][24] bf16 (rows padded so the
+// fragment loads of 8 rows x 4 lanes hit 32 distinct banks)
+constexpr int kSpinBytes = kWin * kNPos;                      // 800
+constexpr int kRingBytes = 3 * kSlots * kWin * kRowH * 2;     // 13824
+constexpr int kWarpSmem = kSpinBytes + kRingBytes;            // 14624 (multiple of 16)
 
 // (dy, dx) of the "mask B" taps and of the layer-1 features
 __constant__ int8_t c_tapB[5][2] = {{-1, -1}, {-1, 0}, {-1, 1}, {0, -1}, {0, 0}};
@@ -88,10 +93,12 @@ struct NetPtrs {
 };
 
 // ---------------------------------------------------------------------------
-// Sequential forward over the 100 window positions for 16 windows per warp.
-// MODE 0 scores given windows (teacher forcing); MODE 1 samples the interior.
-// Writes lq[w] = log q(window w) (fp32 sum), and optionally the logits z[w][p]
-// and the activations h[l][w][p][c] (training).
+// Sequential forward over the 100 window positions for 8 windows per warp
+// (rows 0..7 of each m16 tile; rows 8..15 are zero).  MODE 0 scores given
+// windows (teacher forcing); MODE 1 samples the interior.  Writes lq[w] =
+// log q(window w) (fp32 sum), and optionally the logits z[w][p] and the
+// activations h[l][w][p][c] (training).  Layers 2-4 accumulate their five taps
+// in two independent chains (taps 0, 2, 4 and taps 1, 3) summed at the end.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int8_t* win, int n, float* lq,
@@ -100,14 +107,14 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int w0 = (blockIdx.x * kWarpsFwd + warp) * 16;
+    const int w0 = (blockIdx.x * kWarpsFwd + warp) * kWin;
     if (w0 >= n) return;
     int8_t* sp = reinterpret_cast<int8_t*>(smem + warp * kWarpSmem);
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(smem + warp * kWarpSmem + kSpinBytes);
     auto H = [&](int layer, int slot, int row) -> __nv_bfloat16* {
-        return ring + ((layer * kSlots + slot) * 16 + row) * kC;
+        return ring + ((layer * kSlots + slot) * kWin + row) * kRowH;
     };
-    for (int i = lane; i < 16 * kNPos; i += 32) {
+    for (int i = lane; i < kWin * kNPos; i += 32) {
         const int row = i / kNPos;
         sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
     }
@@ -134,7 +141,16 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
             bias[2][nt][e] = net.wf[kOffB3 + co];
         }
     const float b4 = net.wf[kOffB4];
-    float lq_acc[2] = {0.0f, 0.0f};
+    // this thread's four layer-1 features: k = 2tq, 2tq+1, 2tq+8, 2tq+9
+    int fdy[4], fdx[4], fkind[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 2 * tq + (e & 1) + ((e >> 1) ? 8 : 0);
+        fdy[e] = c_feat[k][0];
+        fdx[e] = c_feat[k][1];
+        fkind[e] = c_feat[k][2];
+    }
+    float lq_acc = 0.0f;
     __syncwarp();
 
     for (int p = 0; p < kNPos; ++p) {
@@ -142,34 +158,29 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
         // ---- layer 1: features (mask A interior taps + ring taps) ----
         uint32_t a[4];
         {
-            float f[2][4];
+            const int8_t* s = sp + g * kNPos;
+            float f[4];
 #pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int8_t* s = sp + (g + 8 * rr) * kNPos;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 2 * tq + (e & 1) + ((e >> 1) ? 8 : 0);
-                    const int kind = c_feat[k][2];
-                    const int yy = r + c_feat[k][0], xx = c + c_feat[k][1];
-                    float v = 0.0f;
-                    if (kind != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
-                        const bool in = interior(yy, xx);
-                        if ((kind == 0) == in) v = (float)s[yy * kS + xx];
-                    }
-                    f[rr][e] = v;
+            for (int e = 0; e < 4; ++e) {
+                const int yy = r + fdy[e], xx = c + fdx[e];
+                float v = 0.0f;
+                if (fkind[e] != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
+                    const bool in = interior(yy, xx);
+                    if ((fkind[e] == 0) == in) v = (float)s[yy * kS + xx];
                 }
+                f[e] = v;
             }
-            a[0] = pack_bf16(f[0][0], f[0][1]);
-            a[1] = pack_bf16(f[1][0], f[1][1]);
-            a[2] = pack_bf16(f[0][2], f[0][3]);
-            a[3] = pack_bf16(f[1][2], f[1][3]);
+            a[0] = pack_bf16(f[0], f[1]);
+            a[1] = 0u;
+            a[2] = pack_bf16(f[2], f[3]);
+            a[3] = 0u;
         }
 #pragma unroll
         for (int layer = 0; layer < 3; ++layer) {
-            float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            float d[2][2][4] = {};
             if (layer == 0) {
-                mma16816(d[0], a, bw1[0]);
-                mma16816(d[1], a, bw1[1]);
+                mma16816(d[0][0], a, bw1[0]);
+                mma16816(d[0][1], a, bw1[1]);
             } else {
 #pragma unroll
                 for (int t = 0; t < 5; ++t) {
@@ -177,90 +188,295 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
                     if (yy < 0 || xx < 0 || xx >= kS) continue;
                     const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
                     const __nv_bfloat16* h0 = H(layer - 1, sl, g);
-                    const __nv_bfloat16* h8 = H(layer - 1, sl, g + 8);
                     uint32_t at[4];
                     at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
-                    at[1] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq);
+                    at[1] = 0u;
                     at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
-                    at[3] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq + 8);
-                    if (layer == 1) { mma16816(d[0], at, bw2[t][0]); mma16816(d[1], at, bw2[t][1]); }
-                    else { mma16816(d[0], at, bw3[t][0]); mma16816(d[1], at, bw3[t][1]); }
+                    at[3] = 0u;
+                    if (layer == 1) { mma16816(d[t & 1][0], at, bw2[t][0]); mma16816(d[t & 1][1], at, bw2[t][1]); }
+                    else { mma16816(d[t & 1][0], at, bw3[t][0]); mma16816(d[t & 1][1], at, bw3[t][1]); }
                 }
             }
             // bias, relu, bf16 into the ring (and the activation output)
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 const int co = nt * 8 + 2 * tq;
-                const uint32_t v0 = pack_bf16(fmaxf(d[nt][0] + bias[layer][nt][0], 0.f),
-                                              fmaxf(d[nt][1] + bias[layer][nt][1], 0.f));
-                const uint32_t v8 = pack_bf16(fmaxf(d[nt][2] + bias[layer][nt][0], 0.f),
-                                              fmaxf(d[nt][3] + bias[layer][nt][1], 0.f));
+                const uint32_t v0 = pack_bf16(fmaxf((d[0][nt][0] + d[1][nt][0]) + bias[layer][nt][0], 0.f),
+                                              fmaxf((d[0][nt][1] + d[1][nt][1]) + bias[layer][nt][1], 0.f));
                 *reinterpret_cast<uint32_t*>(H(layer, slot, g) + co) = v0;
-                *reinterpret_cast<uint32_t*>(H(layer, slot, g + 8) + co) = v8;
-                if (h_out) {
-                    if (w0 + g < n)
-                        *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g) * kNPos + p) * kC + co) = v0;
-                    if (w0 + g + 8 < n)
-                        *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g + 8) * kNPos + p) * kC + co) = v8;
-                }
+                if (h_out && w0 + g < n)
+                    *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g) * kNPos + p) * kC + co) = v0;
             }
             __syncwarp();
         }
         // ---- layer 4: the logit ----
-        float d4[4] = {0.f, 0.f, 0.f, 0.f};
+        float d4[2][4] = {};
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
             const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
             if (yy < 0 || xx < 0 || xx >= kS) continue;
             const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
             const __nv_bfloat16* h0 = H(2, sl, g);
-            const __nv_bfloat16* h8 = H(2, sl, g + 8);
             uint32_t at[4];
             at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
-            at[1] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq);
+            at[1] = 0u;
             at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
-            at[3] = *reinterpret_cast<const uint32_t*>(h8 + 2 * tq + 8);
-            mma16816(d4, at, bw4[t]);
+            at[3] = 0u;
+            mma16816(d4[t & 1], at, bw4[t]);
         }
-        if (tq == 0) {   // column 0 of the C fragment: rows g and g + 8
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int row = g + 8 * rr, w = w0 + row;
-                const float z = (rr ? d4[2] : d4[0]) + b4;
-                if (w < n) {
-                    if (z_out) z_out[(size_t)w * kNPos + p] = z;
-                    if (interior(r, c)) {
-                        int8_t x = sp[row * kNPos + p];
-                        if (MODE == 1) {
-                            const LearnedKey k = keys[w];
-                            const int i = (r - 1) * kP + (c - 1);
-                            const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
-                            const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
-                            const float sg = 1.0f / (1.0f + expf(-z));
-                            const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
-                            x = (u < thr) ? (int8_t)1 : (int8_t)-1;
-                            sp[row * kNPos + p] = x;
-                        }
-                        lq_acc[rr] += log_sigmoid((float)x * z);
+        if (tq == 0) {   // column 0 of the C fragment, row g = window w0 + g
+            const int w = w0 + g;
+            const float z = (d4[0][0] + d4[1][0]) + b4;
+            if (w < n) {
+                if (z_out) z_out[(size_t)w * kNPos + p] = z;
+                if (interior(r, c)) {
+                    int8_t x = sp[g * kNPos + p];
+                    if (MODE == 1) {
+                        const LearnedKey k = keys[w];
+                        const int i = (r - 1) * kP + (c - 1);
+                        const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
+                        const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
+                        const float sg = 1.0f / (1.0f + expf(-z));
+                        const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
+                        x = (u < thr) ? (int8_t)1 : (int8_t)-1;
+                        sp[g * kNPos + p] = x;
                     }
+                    lq_acc += log_sigmoid((float)x * z);
                 }
             }
         }
         __syncwarp();
     }
-    if (tq == 0) {
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int w = w0 + g + 8 * rr;
-            if (w < n) lq[w] = lq_acc[rr];
-        }
-    }
+    if (tq == 0 && w0 + g < n) lq[w0 + g] = lq_acc;
     if (MODE == 1) {
-        for (int i = lane; i < 16 * kNPos; i += 32) {
+        for (int i = lane; i < kWin * kNPos; i += 32) {
             const int row = i / kNPos;
             if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// FP8 (E4M3) inference variant of the sequential forward: weights enter as
+// e4m3(W * s_l) with a per-layer power-of-two scale s_l, activations as
+// e4m3(relu(.)) (satfinite, round to nearest even), products summed in fp32
+// by mma.sync.m16n8k32 e4m3 x e4m3 -> f32 and divided by s_l.  K = 32 covers
+// two taps per k-step (taps 0+1, 2+3, 4+zero); layer 1's 16 features fill
+// the first half of one k-step.  Same window layout and outputs as the BF16
+// kernel (no activation output: inference only).
+// ---------------------------------------------------------------------------
+constexpr int kRowQ = 16;                                     // fp8 per activation row (conflict-free as is)
+constexpr int kRingQBytes = 3 * kSlots * kWin * kRowQ;        // 4608
+constexpr int kWarpSmemQ = kSpinBytes + kRingQBytes;          // 5408 (multiple of 16)
+
+__device__ __forceinline__ void mma16832_e4m3(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack4_fp8(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+// B fragment (K x N = 32 x 8, 8-bit) from the fp8 weight copy: k = 4*(lane%4)
+// + {0..3} and 16 + that, n = lane/4.  wk(k, n) returns the byte of row k.
+template <typename F>
+__device__ __forceinline__ void load_b8(F wk, uint32_t (&b)[2]) {
+    const int lane = threadIdx.x & 31, k = 4 * (lane & 3), n = lane >> 2;
+    uint32_t r0 = 0, r1 = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        r0 |= (uint32_t)wk(k + e, n) << (8 * e);
+        r1 |= (uint32_t)wk(16 + k + e, n) << (8 * e);
+    }
+    b[0] = r0;
+    b[1] = r1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_fp8_kernel(const uint8_t* wq, const float* wscale,
+                                                                     const float* wf, int8_t* win, int n, float* lq,
+                                                                     float* z_out, const LearnedKey* keys,
+                                                                     uint32_t round_t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int w0 = (blockIdx.x * kWarpsFwd + warp) * kWin;
+    if (w0 >= n) return;
+    int8_t* sp = reinterpret_cast<int8_t*>(smem + warp * kWarpSmemQ);
+    uint8_t* ring = smem + warp * kWarpSmemQ + kSpinBytes;
+    auto H = [&](int layer, int slot, int row) -> uint8_t* {
+        return ring + ((layer * kSlots + slot) * kWin + row) * kRowQ;
+    };
+    for (int i = lane; i < kWin * kNPos; i += 32) {
+        const int row = i / kNPos;
+        sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
+    }
+    // B fragments: layer 1 (k = feature < 16), layers 2/3 (k-step s: taps 2s, 2s+1), layer 4 (N = 1)
+    uint32_t bq1[2][2], bq2[3][2][2], bq3[3][2][2], bq4[3][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        load_b8([&](int k, int nn) -> uint8_t { return k < 16 ? wq[kOffW1 + k * kC + nt * 8 + nn] : 0; }, bq1[nt]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            load_b8([&](int k, int nn) -> uint8_t {
+                const int t = 2 * s + (k >> 4), ci = k & 15;
+                return t < 5 ? wq[kOffW2 + t * 256 + ci * kC + nt * 8 + nn] : 0;
+            }, bq2[s][nt]);
+            load_b8([&](int k, int nn) -> uint8_t {
+                const int t = 2 * s + (k >> 4), ci = k & 15;
+                return t < 5 ? wq[kOffW3 + t * 256 + ci * kC + nt * 8 + nn] : 0;
+            }, bq3[s][nt]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+        load_b8([&](int k, int nn) -> uint8_t {
+            const int t = 2 * s + (k >> 4), ci = k & 15;
+            return (t < 5 && nn == 0) ? wq[kOffW4 + t * kC + ci] : 0;
+        }, bq4[s]);
+    const float inv_s[4] = {1.0f / wscale[0], 1.0f / wscale[1], 1.0f / wscale[2], 1.0f / wscale[3]};
+    float bias[3][2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int co = nt * 8 + 2 * tq + e;
+            bias[0][nt][e] = wf[kOffB1 + co];
+            bias[1][nt][e] = wf[kOffB2 + co];
+            bias[2][nt][e] = wf[kOffB3 + co];
+        }
+    const float b4 = wf[kOffB4];
+    // this thread's four layer-1 features: k = 4tq .. 4tq+3
+    int fdy[4], fdx[4], fkind[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 4 * tq + e;
+        fdy[e] = c_feat[k][0];
+        fdx[e] = c_feat[k][1];
+        fkind[e] = c_feat[k][2];
+    }
+    float lq_acc = 0.0f;
+    __syncwarp();
+
+    for (int p = 0; p < kNPos; ++p) {
+        const int r = p / kS, c = p - r * kS, slot = p % kSlots;
+        uint32_t a[4];
+        {
+            const int8_t* s = sp + g * kNPos;
+            float f[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int yy = r + fdy[e], xx = c + fdx[e];
+                float v = 0.0f;
+                if (fkind[e] != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
+                    const bool in = interior(yy, xx);
+                    if ((fkind[e] == 0) == in) v = (float)s[yy * kS + xx];
+                }
+                f[e] = v;
+            }
+            a[0] = pack4_fp8(f[0], f[1], f[2], f[3]);
+            a[1] = 0u;
+            a[2] = 0u;
+            a[3] = 0u;
+        }
+#pragma unroll
+        for (int layer = 0; layer < 3; ++layer) {
+            float d[2][2][4] = {};
+            if (layer == 0) {
+                mma16832_e4m3(d[0][0], a, bq1[0]);
+                mma16832_e4m3(d[0][1], a, bq1[1]);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    uint32_t at[4] = {0u, 0u, 0u, 0u};
+                    bool any = false;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = 2 * s + h;
+                        if (t >= 5) continue;
+                        const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+                        if (yy < 0 || xx < 0 || xx >= kS) continue;
+                        const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
+                        at[2 * h] = *reinterpret_cast<const uint32_t*>(H(layer - 1, sl, g) + 4 * tq);
+                        any = true;
+                    }
+                    if (!any) continue;
+                    if (layer == 1) { mma16832_e4m3(d[s & 1][0], at, bq2[s][0]); mma16832_e4m3(d[s & 1][1], at, bq2[s][1]); }
+                    else { mma16832_e4m3(d[s & 1][0], at, bq3[s][0]); mma16832_e4m3(d[s & 1][1], at, bq3[s][1]); }
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int co = nt * 8 + 2 * tq;
+                const float v0 = fmaxf((d[0][nt][0] + d[1][nt][0]) * inv_s[layer] + bias[layer][nt][0], 0.f);
+                const float v1 = fmaxf((d[0][nt][1] + d[1][nt][1]) * inv_s[layer] + bias[layer][nt][1], 0.f);
+                const unsigned short q = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+                *reinterpret_cast<unsigned short*>(H(layer, slot, g) + co) = q;
+            }
+            __syncwarp();
+        }
+        float d4[2][4] = {};
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            uint32_t at[4] = {0u, 0u, 0u, 0u};
+            bool any = false;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = 2 * s + h;
+                if (t >= 5) continue;
+                const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
+                if (yy < 0 || xx < 0 || xx >= kS) continue;
+                const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
+                at[2 * h] = *reinterpret_cast<const uint32_t*>(H(2, sl, g) + 4 * tq);
+                any = true;
+            }
+            if (any) mma16832_e4m3(d4[s & 1], at, bq4[s]);
+        }
+        if (tq == 0) {
+            const int w = w0 + g;
+            const float z = (d4[0][0] + d4[1][0]) * inv_s[3] + b4;
+            if (w < n) {
+                if (z_out) z_out[(size_t)w * kNPos + p] = z;
+                if (interior(r, c)) {
+                    int8_t x = sp[g * kNPos + p];
+                    if (MODE == 1) {
+                        const LearnedKey k = keys[w];
+                        const int i = (r - 1) * kP + (c - 1);
+                        const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
+                        const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
+                        const float sg = 1.0f / (1.0f + expf(-z));
+                        const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
+                        x = (u < thr) ? (int8_t)1 : (int8_t)-1;
+                        sp[g * kNPos + p] = x;
+                    }
+                    lq_acc += log_sigmoid((float)x * z);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (tq == 0 && w0 + g < n) lq[w0 + g] = lq_acc;
+    if (MODE == 1) {
+        for (int i = lane; i < kWin * kNPos; i += 32) {
+            const int row = i / kNPos;
+            if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];
+        }
+    }
+}
+
+// fp8 weight copy: e4m3(W * s_layer) for the weights of each layer (biases
+// stay fp32 and are read from the masters).
+__global__ void to_fp8_kernel(const float* w, const float* wscale, uint8_t* wq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    const int layer = i < kOffW2 ? 0 : i < kOffW3 ? 1 : i < kOffW4 ? 2 : 3;
+    wq[i] = __nv_cvt_float_to_fp8(w[i] * wscale[layer], __NV_SATFINITE, __NV_E4M3);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,7 +732,7 @@ __global__ void mh_apply_kernel(DevState st, const LearnedLat* ll, int n_lat, in
 // ---------------------------------------------------------------------------
 // launch wrappers (used by the C ABI below)
 // ---------------------------------------------------------------------------
-static int fwd_blocks(int n) { return (n + 16 * kWarpsFwd - 1) / (16 * kWarpsFwd); }
+static int fwd_blocks(int n) { return (n + kWin * kWarpsFwd - 1) / (kWin * kWarpsFwd); }
 
 cudaError_t configure_learned_kernels() {
     cudaError_t e = cudaFuncSetAttribute(ar_net_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -535,6 +751,27 @@ cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, flo
     NetPtrs np{ns.wb, ns.w};
     ar_net_kernel<0><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(
         np, const_cast<int8_t*>(win), n, lq, z, h, nullptr, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_forward_fp8(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
+                                   cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    ar_net_fp8_kernel<0><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmemQ, stream>>>(
+        ns.wq, ns.wscale, ns.w, const_cast<int8_t*>(win), n, lq, z, nullptr, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_sample_fp8(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
+                                  uint32_t round_t, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    ar_net_fp8_kernel<1><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmemQ, stream>>>(
+        ns.wq, ns.wscale, ns.w, win, n, lq, nullptr, keys, round_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_fp8(const NetState& ns, cudaStream_t stream) {
+    to_fp8_kernel<<<(kNParams + 255) / 256, 256, 0, stream>>>(ns.w, ns.wscale, ns.wq);
     return cudaGetLastError();
 }
 

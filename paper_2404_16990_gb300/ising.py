@@ -108,6 +108,7 @@ def _load():
             "ising_learned_round": ([vp, vp, i64, i64p], ctypes.c_int),
             "ising_snapshot": ([vp, vp, sz], ctypes.c_int),
             "ising_net_accepted": ([vp, i64p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ising_net_set_precision": ([vp, ctypes.c_int], ctypes.c_int),
             "ising_binder": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -343,6 +344,8 @@ def ising_tau_int(x, c: float = 6.0):
 
 
 ISING_NET_PARAMS = 2945
+ISING_NET_BF16 = 0
+ISING_NET_FP8 = 1
 
 
 class IsingNet:
@@ -366,6 +369,9 @@ class IsingNet:
         p = np.ascontiguousarray(params, dtype=np.float32)
         assert p.size == ISING_NET_PARAMS
         _check(_load().ising_net_set_params(self.h, _ptr(p, ctypes.c_float)))
+
+    def set_precision(self, precision: int) -> None:
+        _check(_load().ising_net_set_precision(self.h, precision))
 
     def get_params(self) -> np.ndarray:
         p = np.zeros(ISING_NET_PARAMS, dtype=np.float32)

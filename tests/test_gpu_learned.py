@@ -89,14 +89,16 @@ def test_sample_matches_oracle_except_near_ties():
     assert mism <= 2
 
 
-def _round_compare(L, T, seed, rnd, flat, gain_note=""):
+def _round_compare(L, T, seed, rnd, flat, prec="bf16"):
     sim = ising.IsingSim(L, [T], seed)
     s0 = oracle.init(L, seed, 0)
     net = ising.IsingNet(max_windows=(L // 16) ** 2, max_lattices=1)
     net.set_params(flat)
+    if prec == "fp8":
+        net.set_precision(ising.ISING_NET_FP8)
     acc = sim.learned_round(net, rnd)
     so = s0.copy()
-    acc_o, dE, dM, recs = ol.learned_round(so, flat, T, seed, 0, rnd)
+    acc_o, dE, dM, recs = ol.learned_round(so, flat, T, seed, 0, rnd, prec=prec)
     gs = sim.spins(0)
     origins = ol.patch_origins(L, rnd)
     bad = 0
@@ -178,3 +180,25 @@ def test_async_rounds_match_synchronous_rounds():
     assert np.array_equal(nb.accepted(2), tot) and tot.sum() > 0
     for i in range(2):
         assert np.array_equal(a.spins(i), b.spins(i))
+
+
+def test_fp8_score_matches_oracle():
+    net = ising.IsingNet(max_windows=128)
+    flat = ol.init_params(29, gain=1.5)
+    net.set_params(flat)
+    win = rand_windows(45, 8)
+    lq16, z16 = net.score(win, with_z=True)
+    net.set_precision(ising.ISING_NET_FP8)
+    lq8, z8 = net.score(win, with_z=True)
+    zo, _ = ol.forward(win, flat, prec="fp8")
+    inner = ol.interior_mask(10).ravel()
+    dz = np.abs(z8[:, inner] - zo.reshape(45, 100)[:, inner])
+    assert np.median(dz) < 1e-3 and dz.max() < 0.5, (np.median(dz), dz.max())
+    assert np.abs(z8 - z16)[:, inner].max() > 1e-3          # the precision really changed
+    assert np.allclose(lq8, ol.log_q(win, zo), atol=0.5, rtol=1e-2)
+
+
+@pytest.mark.parametrize("rnd", [0, 1])
+def test_fp8_learned_round_matches_oracle(rnd):
+    flat = ol.init_params(31, gain=0.3)
+    _round_compare(64, 3.5, 202, rnd, flat, prec="fp8")

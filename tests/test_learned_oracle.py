@@ -150,3 +150,31 @@ def test_learned_round_runs_and_keeps_energy_bookkeeping():
     assert len(recs) == (L // 16) ** 2
     assert oracle.energy(s) - e0 == dE and oracle.magnetization(s) - m0 == dM
     assert acc == sum(r["accept"] for r in recs)
+
+
+def test_e4m3_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8_e4m3fn")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.standard_normal(20000) * 10 ** rng.uniform(-4, 2.4, 20000),
+                        [0.0, 448.0, -448.0, 2 ** -9, 3 * 2 ** -10, 1.0625, 1.1875, 240.0, 0.015625]])
+    x = x[np.abs(x) <= 448].astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(ol.e4m3(x.astype(np.float64)), ref)
+    assert ol.e4m3(np.array([1000.0, -1e6]))[0] == 448.0          # saturating
+
+
+def test_fp8_forward_is_close_to_bf16_and_keeps_the_mask():
+    win = rand_windows(8, 10, 3)
+    flat = ol.init_params(5, gain=1.0)
+    z8, _ = ol.forward(win, flat, prec="fp8")
+    z16, _ = ol.forward(win, flat)
+    inner = ol.interior_mask(10)
+    assert np.median(np.abs(z8 - z16)[:, inner]) < 0.1
+    w2 = win.copy()
+    w2[:, 4, 4] *= -1
+    z8b, _ = ol.forward(w2, flat, prec="fp8")
+    order = np.arange(100).reshape(10, 10)
+    before = order <= order[4, 4]
+    assert np.array_equal(z8[:, before], z8b[:, before])
