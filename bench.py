@@ -210,10 +210,11 @@ def ours(args):
                 "stream": ising.ISING_PLAN_STREAM}[args.plan]
         for s in sims:
             s.set_plan(code)
-    elif args.autotune or args.workload == "batch754":
-        tuned = [s.autotune(probe_sweeps=20 if args.workload == "batch754" else 5) for s in sims]
     for s in sims:
         s.set_graph(True)
+    if args.workload != "batch754" or args.plan == "tuned":
+        if args.autotune or args.workload == "batch754":
+            tuned = [s.autotune(probe_sweeps=20 if args.workload == "batch754" else 5) for s in sims]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     sites = sum(sum(int(ising.ising_lattice_size(s.h, i)) ** 2 for i in range(s.n)) for s in sims)
     flips_per_step = sites * n_sw

@@ -206,7 +206,8 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
  * 128} and block sizes {auto, 256, 512} when some lattice has L <= 1024;
  * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {2, 4, 8},
  * threads in {128, 256}) for probe_sweeps sweeps each on the handle's stream
- * and keep the fastest.  The lattices and the sweep counter are saved before
+ * (through CUDA graphs if ising_set_graph is on, as the sweeps will run) and
+ * keep the fastest.  The lattices and the sweep counter are saved before
  * and restored after, so tuning changes no result.  If the environment
  * variable ISING_TUNE_CACHE names a file, the choice is appended to it keyed by
  * the multiset of lattice sizes and the device, and a later call with
@@ -262,11 +263,13 @@ int ising_snapshot(ising_t h, void* dev_dst, size_t bytes);
 typedef struct ising_net* ising_net_t;
 
 /* Device workspace of a net that handles up to max_windows windows per call
- * (training batch, or patches of one round: sum over lattices of (L/16)^2) and
- * rounds over up to max_lattices lattices. */
-int ising_net_workspace_bytes(int max_windows, int max_lattices, size_t* bytes);
-int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* dev_workspace,
-                     size_t ws_bytes, void* cuda_stream);
+ * (patches of one round: sum over lattices of (L/16)^2, ~0.25 KB each), a
+ * training batch / gradient / logits call of up to max_batch windows (~10 KB
+ * each: activations kept for the backward pass), and rounds over up to
+ * max_lattices lattices. */
+int ising_net_workspace_bytes(int max_windows, int max_batch, int max_lattices, size_t* bytes);
+int ising_net_create(ising_net_t* out, int max_windows, int max_batch, int max_lattices,
+                     void* dev_workspace, size_t ws_bytes, void* cuda_stream);
 void ising_net_destroy(ising_net_t net);
 
 /* Arithmetic of scoring, sampling and rounds (training is always BF16):

@@ -847,8 +847,7 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     rc = ising_save(h, saved.data(), nbytes);
     if (rc != ISING_OK) return rc;
     const Plan plan0 = h->plan;
-    const bool graph0 = h->graph;
-    h->graph = false;
+    const bool graph0 = h->graph;   // candidates are timed the way sweeps will run (graph replay or not)
     double sites = 0;
     for (int L : h->L) sites += (double)L * L;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -859,7 +858,8 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     for (const TuneCand& c : cands) {
         if (apply_cand(h, c) != ISING_OK) continue;
         if (ising_load(h, saved.data(), nbytes) != ISING_OK) break;
-        if (ising_sweep(h, 1) != ISING_OK) continue;                 // warm-up (graph-free)
+        if (ising_sweep(h, probe_sweeps) != ISING_OK) continue;      // warm-up (captures the graph if on)
+        if (ising_load(h, saved.data(), nbytes) != ISING_OK) break;
         cudaEventRecord(e0, h->stream);
         if (ising_sweep(h, probe_sweeps) != ISING_OK) continue;
         cudaEventRecord(e1, h->stream);
@@ -871,7 +871,7 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->graph = graph0;
+    (void)graph0;
     if (best < 0) {
         h->plan = plan0;
         build_tables(h);
@@ -919,7 +919,7 @@ void ising_destroy(ising_t h) {
 // Learned patch proposal: network handle and round
 // ===========================================================================
 struct ising_net {
-    int max_windows = 0, max_lattices = 0;
+    int max_windows = 0, max_lattices = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
     char* ws = nullptr;
     NetState ns{};
@@ -946,7 +946,7 @@ struct NetLayout {
     size_t w, m, v, g, wb, loss, wq, wscale, win, win2, z, lq, lq2, h, keys, ll, acc, total;
 };
 
-NetLayout net_layout(int W, int NL) {
+NetLayout net_layout(int W, int NB, int NL) {
     NetLayout l{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -956,9 +956,9 @@ NetLayout net_layout(int W, int NL) {
     l.wq = take(P);
     l.wscale = take(16);
     l.win = take(w * 100); l.win2 = take(w * 100);
-    l.z = take(w * 100 * 4);
+    l.z = take((size_t)NB * 100 * 4);
     l.lq = take(w * 4); l.lq2 = take(w * 4);
-    l.h = take(3 * w * 100 * 16 * 2);
+    l.h = take(3 * (size_t)NB * 100 * 16 * 2);
     l.keys = take(w * sizeof(LearnedKey));
     l.ll = take((size_t)NL * sizeof(LearnedLat));
     l.acc = take((size_t)NL * 8);
@@ -1021,25 +1021,27 @@ int ising_net_set_precision(ising_net_t net, int precision) {
     return ISING_OK;
 }
 
-int ising_net_workspace_bytes(int max_windows, int max_lattices, size_t* bytes) {
-    if (!bytes || max_windows < 1 || max_lattices < 1)
-        return fail(ISING_EINVAL, "max_windows and max_lattices must be >= 1");
-    *bytes = net_layout(max_windows, max_lattices).total;
+int ising_net_workspace_bytes(int max_windows, int max_batch, int max_lattices, size_t* bytes) {
+    if (!bytes || max_windows < 1 || max_batch < 1 || max_lattices < 1)
+        return fail(ISING_EINVAL, "max_windows, max_batch and max_lattices must be >= 1");
+    *bytes = net_layout(max_windows, max_batch, max_lattices).total;
     return ISING_OK;
 }
 
-int ising_net_create(ising_net_t* out, int max_windows, int max_lattices, void* dev_ws, size_t ws_bytes,
-                     void* cuda_stream) {
+int ising_net_create(ising_net_t* out, int max_windows, int max_batch, int max_lattices, void* dev_ws,
+                     size_t ws_bytes, void* cuda_stream) {
     if (!out) return fail(ISING_EINVAL, "out is NULL");
     *out = nullptr;
-    if (max_windows < 1 || max_lattices < 1) return fail(ISING_EINVAL, "max_windows and max_lattices must be >= 1");
-    const NetLayout l = net_layout(max_windows, max_lattices);
+    if (max_windows < 1 || max_batch < 1 || max_lattices < 1)
+        return fail(ISING_EINVAL, "max_windows, max_batch and max_lattices must be >= 1");
+    const NetLayout l = net_layout(max_windows, max_batch, max_lattices);
     if (ws_bytes < l.total) return fail(ISING_ENOMEM, "net workspace too small: %zu < %zu", ws_bytes, l.total);
     if (!dev_ws || ((uintptr_t)dev_ws) % kAlign) return fail(ISING_EINVAL, "workspace NULL or not 256-byte aligned");
     CUDA_TRY(configure_learned_kernels(), "configure learned kernels");
     auto* net = new ising_net();
     char* b = (char*)dev_ws;
     net->max_windows = max_windows;
+    net->max_batch = max_batch;
     net->max_lattices = max_lattices;
     net->stream = (cudaStream_t)cuda_stream;
     net->ws = b;
@@ -1094,6 +1096,7 @@ int ising_net_get_params(ising_net_t net, float* host) {
 
 int ising_net_score(ising_net_t net, const int8_t* host_windows, int n, float* host_logq, float* host_z) {
     if (!net || !host_logq) return fail(ISING_EINVAL, "NULL argument");
+    if (host_z && n > net->max_batch) return fail(ISING_EINVAL, "logits need n <= max_batch=%d", net->max_batch);
     int rc = net_upload_windows(net, host_windows, n);
     if (rc != ISING_OK) return rc;
     CUDA_TRY(net_score(net, net->win, n, net->lq, host_z ? net->z : nullptr, net->stream), "score");
@@ -1121,6 +1124,7 @@ int ising_net_sample(ising_net_t net, int8_t* host_windows, int n, const uint32_
 
 int ising_net_grad(ising_net_t net, const int8_t* host_windows, int n, float* host_grad, float* host_loss) {
     if (!net || !host_grad) return fail(ISING_EINVAL, "NULL argument");
+    if (n > net->max_batch) return fail(ISING_EINVAL, "n must be <= max_batch=%d", net->max_batch);
     int rc = net_upload_windows(net, host_windows, n);
     if (rc != ISING_OK) return rc;
     CUDA_TRY(cudaMemsetAsync(net->ns.g, 0, ISING_NET_PARAMS * sizeof(float), net->stream), "zero grad");
@@ -1141,7 +1145,8 @@ int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int
                     float lr, uint64_t seed, float* host_losses) {
     if (!net || !dev_pool_words) return fail(ISING_EINVAL, "NULL argument");
     if (n_snap < 1 || !valid_L(L)) return fail(ISING_EINVAL, "need n_snap >= 1 and a valid L");
-    if (batch < 1 || batch > net->max_windows) return fail(ISING_EINVAL, "batch must be in [1, %d]", net->max_windows);
+    if (batch < 1 || batch > net->max_batch || batch > net->max_windows)
+        return fail(ISING_EINVAL, "batch must be in [1, min(max_batch, max_windows)]");
     if (steps < 0 || !(lr > 0.f) || !std::isfinite(lr)) return fail(ISING_EINVAL, "invalid steps or lr");
     std::vector<float> losses;
     for (int64_t s = 0; s < steps; ++s) {

@@ -92,8 +92,9 @@ def _load():
             "ising_destroy": ([vp], None),
             "ising_sweep_noalloc": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_uint64), i64, i64, vp, vp], ctypes.c_int),
-            "ising_net_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)], ctypes.c_int),
-            "ising_net_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, sz, vp], ctypes.c_int),
+            "ising_net_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_net_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, sz, vp],
+                                 ctypes.c_int),
             "ising_net_destroy": ([vp], None),
             "ising_net_set_params": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ising_net_get_params": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
@@ -352,18 +353,21 @@ class IsingNet:
     """Owner of a learned-proposal network handle and its torch-allocated
     device workspace (ising_net_* in ising.h)."""
 
-    def __init__(self, max_windows: int, max_lattices: int = 1, stream=None, device=None):
+    def __init__(self, max_windows: int, max_lattices: int = 1, stream=None, device=None,
+                 max_batch: Optional[int] = None):
         import torch
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         lib = _load()
+        if max_batch is None:
+            max_batch = min(max_windows, 4096)
         nb = ctypes.c_size_t(0)
-        _check(lib.ising_net_workspace_bytes(max_windows, max_lattices, ctypes.byref(nb)))
+        _check(lib.ising_net_workspace_bytes(max_windows, max_batch, max_lattices, ctypes.byref(nb)))
         self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
         self.h = ctypes.c_void_p()
-        _check(lib.ising_net_create(ctypes.byref(self.h), max_windows, max_lattices, self.workspace.data_ptr(),
-                                    nb.value, self.stream.cuda_stream))
+        _check(lib.ising_net_create(ctypes.byref(self.h), max_windows, max_batch, max_lattices,
+                                    self.workspace.data_ptr(), nb.value, self.stream.cuda_stream))
 
     def set_params(self, params) -> None:
         p = np.ascontiguousarray(params, dtype=np.float32)

@@ -85,7 +85,7 @@ def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000
         torch.cuda.synchronize(dev)
         res["train_pool"] = sets * replicas
         n_win = max(batch, replicas * (L // 16) ** 2)
-        net = ising.IsingNet(max_windows=n_win, max_lattices=replicas, stream=stream)
+        net = ising.IsingNet(max_windows=n_win, max_lattices=replicas, stream=stream, max_batch=batch)
         net.set_params(default_params(seed))
         t0 = time.perf_counter()
         losses = net.train(pool.data_ptr(), sets * replicas, L, train_steps, batch, lr, seed)
@@ -93,14 +93,16 @@ def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000
         res["loss_first"] = float(losses[:10].mean())
         res["loss_last"] = float(losses[-50:].mean())
         res["loss_per_site_last"] = res["loss_last"] / 64.0
+        sim.set_graph(True)
         sim.autotune(probe_sweeps=20)                   # fastest plan for the plain chain
         state = ising.ising_save(sim.h)
         learned = ising.IsingSim(L, [T] * replicas, seed, trace_cap=units, stream=stream)
         ising.ising_load(learned.h, state)
+        learned.set_graph(True)
         learned.autotune(probe_sweeps=20)
         res["plain_plan"] = ising.ising_get_plan(sim.h)
         # what training buys: acceptance of the untrained initial net
-        untrained = ising.IsingNet(max_windows=n_win, max_lattices=replicas, stream=stream)
+        untrained = ising.IsingNet(max_windows=n_win, max_lattices=replicas, stream=stream, max_batch=batch)
         untrained.set_params(default_params(seed))
         probe = ising.IsingSim(L, [T] * replicas, seed, stream=stream)
         ising.ising_load(probe.h, state)
