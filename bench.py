@@ -60,6 +60,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x of all ranks (the slowest rank's time); x itself when not
+    distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; the job's rate is all
+    ranks' units over the slowest rank's time (per ns)."""
+    return units_per_rank * world_size / (seconds_max * 1e9)
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -249,13 +267,9 @@ def ours(args):
         time.sleep(0.3)
     launches = sum(ising.ising_kernel_launches(s.h) for s in sims) - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = flips_per_step * ws / (ms_per_step * 1e6)
+    value = whole_job_rate(flips_per_step, ws, ms_per_step / 1e3)
 
     # dominant kernel: for the 16384^2 workload the streaming half-sweep (2
     # launches per sweep per handle); for the batch the persistent resident
@@ -296,12 +310,8 @@ def ours(args):
                 Eo, Mo = s.observables()
                 d2h += E.nbytes + M.nbytes + Eo.nbytes + Mo.nbytes
         torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - t0
-        e2e_val = flips_per_step * args.e2e_steps / (wall * 1e9)
-        if ws > 1:
-            t = torch.tensor([wall], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = flips_per_step * ws * args.e2e_steps / (float(t.item()) * 1e9)
+        wall = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e_val = whole_job_rate(flips_per_step * args.e2e_steps, ws, wall)
         e2e = {"value": e2e_val, "unit": "flip/ns", "h2d_bytes_per_step": int(sum(nbytes)),
                "d2h_bytes_per_step": int(d2h)}
 

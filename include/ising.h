@@ -192,20 +192,23 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
  * shared-memory limit, else ISING_EINVAL); STREAM runs one launch per
  * half-sweep over the lattices in device memory.  Tuning knobs (0 = default):
  * words_per_thread in {1, 2, 4} = 32-bit words per streaming thread and row;
- * rows_per_item = rows per streaming thread; sweeps_per_unit = sweeps a
+ * rows_per_item = rows per streaming thread (lowered per lattice so that one tile
+ * of a block never spans more rows than the lattice has); sweeps_per_unit = sweeps a
  * resident work unit runs before its group is stored; threads = block size
  * (a multiple of 32, at most 512 resident / 256 streaming).  No choice
  * changes any result bit. */
 #define ISING_PLAN_AUTO 0
 #define ISING_PLAN_RESIDENT 1
 #define ISING_PLAN_STREAM 2
+#define ISING_PLAN_PERSIST 3
 int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int sweeps_per_unit, int threads);
 
 /* Autotuner: time candidate plans (resident with sweeps_per_unit in {8, 32,
  * 128} and block sizes {auto, 256, 512} when some lattice has L <= 1024;
- * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {2, 4, 8},
- * threads in {128, 256}) for probe_sweeps sweeps each on the handle's stream
+ * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {1, 2, 4, 8},
+ * threads in {128, 256}, and the persistent streaming kernel with the same
+ * tilings) for probe_sweeps sweeps each on the handle's stream
  * (through CUDA graphs if ising_set_graph is on, as the sweeps will run) and
  * keep the fastest.  The lattices and the sweep counter are saved before
  * and restored after, so tuning changes no result.  If the environment

@@ -175,7 +175,7 @@ int build_tables(ising_handle* h) {
                 return fail(ISING_EINVAL, "lattice %d (L=%d) does not fit in shared memory (%zu > %zu bytes)",
                             i, h->L[i], bytes, res_budget);
             res = true;
-        } else if (h->plan.mode == ISING_PLAN_STREAM) {
+        } else if (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST) {
             res = false;
         } else {
             res = h->L[i] <= 1024 && bytes <= res_budget;
@@ -259,8 +259,11 @@ int build_tables(ising_handle* h) {
         s.groups = wn / (uint32_t)V;
         const uint32_t tw = std::min<uint32_t>(s.groups, (uint32_t)B);
         const uint32_t th = (uint32_t)B / tw;
+        // rows per thread: at most R, and no more than keeps a whole tile within the lattice
+        const uint32_t Rl = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)R, (uint32_t)h->L[i] / th));
+        s.rows = Rl;
         const uint32_t tiles_x = (s.groups + tw - 1) / tw;
-        const uint32_t tiles_y = ((uint32_t)h->L[i] + th * R - 1) / (th * R);
+        const uint32_t tiles_y = ((uint32_t)h->L[i] + th * Rl - 1) / (th * Rl);
         s.strips = tiles_y;
         s.item_begin = tiles;
         tiles += (uint64_t)tiles_x * tiles_y;
@@ -269,8 +272,10 @@ int build_tables(ising_handle* h) {
     h->n_slats = (int)slats.size();
     h->total_tiles = tiles;
     if (h->n_slats > 0) {
-        const int occ = stream_occupancy(V, B);
+        const int occ = (h->plan.mode == ISING_PLAN_PERSIST) ? stream_persistent_occupancy(V, B)
+                                                              : stream_occupancy(V, B);
         if (occ <= 0) return fail(ISING_EINVAL, "streaming kernel cannot launch with %d threads", B);
+        // the persistent kernel needs every block co-resident (cooperative launch)
         h->stream_grid = (int)std::min<uint64_t>(tiles, (uint64_t)h->sms * occ);
     }
 
@@ -293,7 +298,8 @@ int build_tables(ising_handle* h) {
 int64_t kernels_per_call(const ising_handle* h, int64_t n) {
     int64_t k = 0;
     if (h->n_groups > 0) k += 1;
-    if (h->n_slats > 0) k += 2 * n;
+    if (h->n_slats > 0 && h->plan.mode == ISING_PLAN_PERSIST) k += 1;
+    else if (h->n_slats > 0) k += 2 * n;
     else if (h->n_groups > 0) k += 1;
     return k;
 }
@@ -308,9 +314,12 @@ int enqueue_sweeps(ising_handle* h, int64_t n) {
         CUDA_TRY(launch_resident(h->st, h->n_groups, n, k, h->res_threads, h->res_grid, h->group_smem,
                                  h->stream), "resident kernel launch");
     }
-    if (h->n_slats > 0) {
-        CUDA_TRY(launch_stream_sweeps(h->st, h->n_slats, h->total_tiles, h->V, std::max(1, h->plan.rows_per_item),
-                                      h->plan.stream_threads, h->stream_grid, n, h->stream),
+    if (h->n_slats > 0 && h->plan.mode == ISING_PLAN_PERSIST) {
+        CUDA_TRY(launch_stream_persistent(h->st, h->n_slats, h->total_tiles, h->V, h->plan.stream_threads,
+                                          h->stream_grid, n, h->stream), "persistent streaming kernel launch");
+    } else if (h->n_slats > 0) {
+        CUDA_TRY(launch_stream_sweeps(h->st, h->n_slats, h->total_tiles, h->V, h->plan.stream_threads,
+                                      h->stream_grid, n, h->stream),
                  "streaming kernel launch");
     } else if (h->n_groups > 0) {
         CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
@@ -728,7 +737,8 @@ int ising_load(ising_t h, const void* buf, size_t bytes) {
 int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item, int sweeps_per_unit,
                    int threads) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
-    if (plan != ISING_PLAN_AUTO && plan != ISING_PLAN_RESIDENT && plan != ISING_PLAN_STREAM)
+    if (plan != ISING_PLAN_AUTO && plan != ISING_PLAN_RESIDENT && plan != ISING_PLAN_STREAM &&
+        plan != ISING_PLAN_PERSIST)
         return fail(ISING_EINVAL, "unknown plan %d", plan);
     if (words_per_thread != 0 && words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4)
         return fail(ISING_EINVAL, "words_per_thread must be 0, 1, 2 or 4");
@@ -741,7 +751,7 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
     p.words_per_thread = words_per_thread;
     p.sweeps_per_unit = sweeps_per_unit;
     p.rows_per_item = rows_per_item ? rows_per_item : 4;
-    if (plan == ISING_PLAN_STREAM) {
+    if (plan == ISING_PLAN_STREAM || plan == ISING_PLAN_PERSIST) {
         if (threads != 0 && threads > 256) return fail(ISING_EINVAL, "streaming kernel allows at most 256 threads");
         p.stream_threads = threads ? threads : 256;
     } else {
@@ -837,8 +847,11 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
         bool ok = true;
         for (int L : h->L) ok &= ((L / 64) % V == 0);
         if (!ok) continue;
-        for (int R : {2, 4, 8})
-            for (int thr : {128, 256}) cands.push_back({ISING_PLAN_STREAM, V, R, 0, thr});
+        for (int R : {1, 2, 4, 8})
+            for (int thr : {128, 256}) {
+                cands.push_back({ISING_PLAN_STREAM, V, R, 0, thr});
+                cands.push_back({ISING_PLAN_PERSIST, V, R, 0, thr});
+            }
     }
     size_t nbytes = 0;
     int rc = ising_state_bytes(h, &nbytes);
@@ -894,7 +907,9 @@ int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_it
     if (words_per_thread) *words_per_thread = h->V;
     if (rows_per_item) *rows_per_item = h->plan.rows_per_item;
     if (sweeps_per_unit) *sweeps_per_unit = h->plan.sweeps_per_unit;
-    if (threads) *threads = h->plan.mode == ISING_PLAN_STREAM ? h->plan.stream_threads : h->res_threads;
+    if (threads)
+        *threads = (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST) ? h->plan.stream_threads
+                                                                                             : h->res_threads;
     return ISING_OK;
 }
 

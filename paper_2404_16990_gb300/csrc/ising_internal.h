@@ -33,9 +33,9 @@ struct GroupDesc {
 // A lattice handled by the streaming kernels, with the prefix of work items.
 struct StreamLat {
     uint32_t lat;        // lattice index
-    uint32_t strips;     // ceil(L / rows_per_item)
+    uint32_t strips;     // tile rows of the lattice
     uint32_t groups;     // wn / words_per_thread
-    uint32_t pad;
+    uint32_t rows;       // rows per thread (clamped so that a tile never exceeds the lattice)
     uint64_t item_begin; // first work item of this lattice
 };
 
@@ -47,7 +47,9 @@ struct Control {
     int error;                   // nonzero: a bounded wait ran out (code in low bits)
     int measure;                 // accumulate moments if nonzero
     long long trace_cap;         // trace entries per lattice (0 = none)
-    unsigned int pad[8];
+    unsigned int bar_count;      // persistent kernel: blocks arrived at the grid barrier
+    unsigned int bar_gen;        // persistent kernel: grid barrier generation
+    unsigned int pad[6];
 };
 
 // Device pointers of one handle, passed by value to kernels.
@@ -98,8 +100,12 @@ cudaError_t launch_resident(const DevState& st, int n_groups, int64_t n_sweeps,
                             int sweeps_per_unit, int threads, int grid, size_t smem_bytes,
                             cudaStream_t stream);
 cudaError_t launch_stream_sweeps(const DevState& st, int n_slats, uint64_t total_items,
-                                 int words_per_thread, int rows_per_item, int threads,
-                                 int grid, int64_t n_sweeps, cudaStream_t stream);
+                                 int words_per_thread, int threads, int grid, int64_t n_sweeps,
+                                 cudaStream_t stream);
+cudaError_t launch_stream_persistent(const DevState& st, int n_slats, uint64_t total_tiles,
+                                     int words_per_thread, int threads, int grid, int64_t n_sweeps,
+                                     cudaStream_t stream);
+int stream_persistent_occupancy(int words_per_thread, int threads);
 cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream);
 
 // Record a message for ising_last_error() and return code (ising_api.cu).

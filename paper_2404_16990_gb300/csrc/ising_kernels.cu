@@ -377,13 +377,12 @@ __device__ __forceinline__ void store_vec(uint32_t* p, const uint32_t (&o)[V]) {
     else { *reinterpret_cast<uint4*>(p) = make_uint4(o[0], o[1], o[2], o[3]); }
 }
 
+// One half-sweep of colour c over the tiles of the streamed lattices, tiles
+// taken in a grid-stride loop; with c == 1 the per-lattice E/M partial sums are
+// reduced per block and added to st.acc.
 template <int V>
-__global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_slats,
-                                                          unsigned long long total_tiles,
-                                                          int R, uint32_t c) {
-    __shared__ unsigned long long red[64];
-    __shared__ int s_last;
-    const unsigned long long t = st.ctl->t;
+__device__ __forceinline__ void stream_tiles(const DevState& st, int n_slats, unsigned long long total_tiles,
+                                             uint32_t c, unsigned long long t, unsigned long long* red) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     unsigned long long sa = 0, sp = 0;
     int cur_slat = -1;
@@ -418,9 +417,10 @@ __global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_
         const uint32_t tile_y = (uint32_t)(local / tiles_x), tile_x = (uint32_t)(local - (unsigned long long)tile_y * tiles_x);
         const uint32_t tx = (uint32_t)tid % tw, ty = (uint32_t)tid / tw;
         const uint32_t kg = tile_x * tw + tx;
-        const uint32_t y0 = (tile_y * th + ty) * (uint32_t)R;
+        const uint32_t R = sl.rows;
+        const uint32_t y0 = (tile_y * th + ty) * R;
         if (ty < th && kg < gw && y0 < L) {
-            const uint32_t y1 = (y0 + (uint32_t)R < L) ? y0 + (uint32_t)R : L;
+            const uint32_t y1 = (y0 + R < L) ? y0 + R : L;
             const uint32_t k0 = kg * V;
             uint32_t* own_base = st.spins + d.word_off + (size_t)c * L * wn;
             const uint32_t* opp = st.spins + d.word_off + (size_t)(1u - c) * L * wn;
@@ -452,15 +452,25 @@ __global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_
         }
     }
 
-    if (c == 1) {
-        if (cur_slat >= 0) {
-            block_sum2(sa, sp, red);
-            if (tid == 0) {
-                const uint32_t lat = st.slats[cur_slat].lat;
-                atomicAdd(&st.acc[2 * lat], sa);
-                atomicAdd(&st.acc[2 * lat + 1], sp);
-            }
+    if (c == 1 && cur_slat >= 0) {
+        block_sum2(sa, sp, red);
+        if (tid == 0) {
+            const uint32_t lat = st.slats[cur_slat].lat;
+            atomicAdd(&st.acc[2 * lat], sa);
+            atomicAdd(&st.acc[2 * lat + 1], sp);
         }
+    }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_slats,
+                                                          unsigned long long total_tiles, uint32_t c) {
+    __shared__ unsigned long long red[64];
+    __shared__ int s_last;
+    const unsigned long long t = st.ctl->t;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    stream_tiles<V>(st, n_slats, total_tiles, c, t, red);
+    if (c == 1) {
         // last block to finish records E/M of every streamed lattice and
         // advances the sweep counter
         __threadfence();
@@ -482,6 +492,66 @@ __global__ void __launch_bounds__(256, 2) stream_half_kernel(DevState st, int n_
             }
         }
     }
+}
+
+// Grid-wide barrier of a cooperative launch (every block co-resident): an
+// arrival counter and a generation word in the control block.  A block that
+// waits longer than the limit sets the error flag and returns false.
+__device__ __forceinline__ bool grid_barrier(Control* ctl) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int g = ld_acquire(&ctl->bar_gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            st_release(&ctl->bar_gen, g + 1u);
+        } else {
+            const unsigned long long start = global_ns();
+            while (ld_acquire(&ctl->bar_gen) == g) {
+                if (global_ns() - start > kWaitLimitNs) {
+                    atomicOr(&ctl->error, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Persistent streaming kernel: n sweeps of every streamed lattice in one
+// cooperative launch, a grid barrier after each half-sweep; after each white
+// half-sweep block 0 records E/M of every lattice.
+template <int V>
+__global__ void __launch_bounds__(256, 2) stream_persist_kernel(DevState st, int n_slats,
+                                                             unsigned long long total_tiles,
+                                                             long long n_sweeps) {
+    __shared__ unsigned long long red[64];
+    const unsigned long long t0 = st.ctl->t;
+    for (long long i = 0; i < n_sweeps; ++i) {
+        const unsigned long long t = t0 + (unsigned long long)i;
+        for (uint32_t c = 0; c < 2; ++c) {
+            stream_tiles<V>(st, n_slats, total_tiles, c, t, red);
+            if (!grid_barrier(st.ctl)) return;
+            if (c == 1 && blockIdx.x == 0) {
+                __threadfence();
+                for (int k = threadIdx.x; k < n_slats; k += blockDim.x) {
+                    const uint32_t lat = st.slats[k].lat;
+                    const unsigned long long a = atomicExch(&st.acc[2 * lat], 0ull);
+                    const unsigned long long p = atomicExch(&st.acc[2 * lat + 1], 0ull);
+                    record(st, lat, st.lat[lat].L, a, p, t);
+                }
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st.ctl->t = t0 + (unsigned long long)n_sweeps;
 }
 
 __global__ void advance_t_kernel(DevState st, long long n) { st.ctl->t += (unsigned long long)n; }
@@ -563,15 +633,15 @@ cudaError_t launch_resident(const DevState& st, int n_groups, int64_t n_sweeps, 
 }
 
 cudaError_t launch_stream_sweeps(const DevState& st, int n_slats, uint64_t total_tiles,
-                                 int words_per_thread, int rows_per_item, int threads, int grid,
+                                 int words_per_thread, int threads, int grid,
                                  int64_t n_sweeps, cudaStream_t stream) {
     if (n_slats <= 0 || n_sweeps <= 0) return cudaSuccess;
     for (int64_t i = 0; i < n_sweeps; ++i) {
         for (uint32_t c = 0; c < 2; ++c) {
             switch (words_per_thread) {
-            case 1: stream_half_kernel<1><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, rows_per_item, c); break;
-            case 2: stream_half_kernel<2><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, rows_per_item, c); break;
-            case 4: stream_half_kernel<4><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, rows_per_item, c); break;
+            case 1: stream_half_kernel<1><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, c); break;
+            case 2: stream_half_kernel<2><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, c); break;
+            case 4: stream_half_kernel<4><<<grid, threads, 0, stream>>>(st, n_slats, total_tiles, c); break;
             default: return cudaErrorInvalidValue;
             }
             cudaError_t e = cudaGetLastError();
@@ -579,6 +649,50 @@ cudaError_t launch_stream_sweeps(const DevState& st, int n_slats, uint64_t total
         }
     }
     return cudaSuccess;
+}
+
+int stream_persistent_occupancy(int words_per_thread, int threads) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (words_per_thread) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stream_persist_kernel<1>, threads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stream_persist_kernel<2>, threads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stream_persist_kernel<4>, threads, 0); break;
+    default: break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+template <int V>
+static cudaError_t launch_persist_v(const DevState& st, int n_slats, uint64_t total_tiles, int threads, int grid,
+                                    int64_t n_sweeps, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stream_persist_kernel<V>, st, n_slats, (unsigned long long)total_tiles,
+                              (long long)n_sweeps);
+}
+
+cudaError_t launch_stream_persistent(const DevState& st, int n_slats, uint64_t total_tiles, int words_per_thread,
+                                     int threads, int grid, int64_t n_sweeps, cudaStream_t stream) {
+    if (n_slats <= 0 || n_sweeps <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(&st.ctl->bar_count, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return e;
+    switch (words_per_thread) {
+    case 1: e = launch_persist_v<1>(st, n_slats, total_tiles, threads, grid, n_sweeps, stream); break;
+    case 2: e = launch_persist_v<2>(st, n_slats, total_tiles, threads, grid, n_sweeps, stream); break;
+    case 4: e = launch_persist_v<4>(st, n_slats, total_tiles, threads, grid, n_sweeps, stream); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream) {

@@ -41,15 +41,17 @@ constexpr int kOffW1 = 0, kOffB1 = 256, kOffW2 = 272, kOffB2 = 1552, kOffW3 = 15
               kOffW4 = 2864, kOffB4 = 2944;
 constexpr int kNParams = ISING_NET_PARAMS;
 static_assert(kOffB4 + 1 == ISING_NET_PARAMS, "parameter layout");
-constexpr int kWarpsFwd = 5;
+constexpr int kWarpsFwd = 4;
 constexpr int kWin = 8;                                       // windows per warp (rows 0..7 of the m16 tile)
 constexpr int kRowH = 24;                                     // bf16 per activation row: 16 + 8 padding
-// per-warp shared memory of the forward kernel: spins [8][100] int8, then the
+// per-warp shared memory of the BF16 forward kernel: spins [8][100] int8, the
 // activation ring [3 layers][12 slots][8 windows][24] bf16 (rows padded so the
-// fragment loads of 8 rows x 4 lanes hit 32 distinct banks)
+// fragment loads of 8 rows x 4 lanes hit 32 distinct banks), and the sampling
+// draws [8][64] u32
 constexpr int kSpinBytes = kWin * kNPos;                      // 800
 constexpr int kRingBytes = 3 * kSlots * kWin * kRowH * 2;     // 13824
-constexpr int kWarpSmem = kSpinBytes + kRingBytes;            // 14624 (multiple of 16)
+constexpr int kDrawBytes = kWin * 64 * 4;                     // 2048
+constexpr int kWarpSmem = kSpinBytes + kRingBytes + kDrawBytes;   // 16672 (multiple of 16)
 
 // (dy, dx) of the "mask B" taps and of the layer-1 features
 __constant__ int8_t c_tapB[5][2] = {{-1, -1}, {-1, 0}, {-1, 1}, {0, -1}, {0, 0}};
@@ -97,8 +99,16 @@ struct NetPtrs {
 // (rows 0..7 of each m16 tile; rows 8..15 are zero).  MODE 0 scores given
 // windows (teacher forcing); MODE 1 samples the interior.  Writes lq[w] =
 // log q(window w) (fp32 sum), and optionally the logits z[w][p] and the
-// activations h[l][w][p][c] (training).  Layers 2-4 accumulate their five taps
-// in two independent chains (taps 0, 2, 4 and taps 1, 3) summed at the end.
+// activations h[l][w][p][c] (training).
+//
+// In the m16n8k16 layout the C fragment a thread holds for an output position
+// (row g, channels 2tq, 2tq+1, 8+2tq, 9+2tq) is exactly the A fragment the next
+// layer needs from that position, so the (0,0) and (0,-1) taps of layers 2-4
+// come from registers; only the three taps of the previous row go through a
+// shared-memory ring written once per position and read about ten positions
+// later.  The sampling draws are made before the position loop, and a sampled
+// spin reaches the other lanes of its window by a shuffle.  Layers 2-4
+// accumulate their taps in two independent chains summed at the end.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int8_t* win, int n, float* lq,
@@ -109,14 +119,28 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
     const int g = lane >> 2, tq = lane & 3;
     const int w0 = (blockIdx.x * kWarpsFwd + warp) * kWin;
     if (w0 >= n) return;
-    int8_t* sp = reinterpret_cast<int8_t*>(smem + warp * kWarpSmem);
-    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(smem + warp * kWarpSmem + kSpinBytes);
+    unsigned char* wbase = smem + warp * kWarpSmem;
+    int8_t* sp = reinterpret_cast<int8_t*>(wbase);
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(wbase + kSpinBytes);
+    uint32_t* draws = reinterpret_cast<uint32_t*>(wbase + kSpinBytes + kRingBytes);   // [8][64]
     auto H = [&](int layer, int slot, int row) -> __nv_bfloat16* {
         return ring + ((layer * kSlots + slot) * kWin + row) * kRowH;
     };
     for (int i = lane; i < kWin * kNPos; i += 32) {
         const int row = i / kNPos;
         sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
+    }
+    if (MODE == 1) {   // the 64 draws of every window: 16 Philox blocks each
+        for (int b = lane; b < kWin * 16; b += 32) {
+            const int row = b >> 4, q = b & 15, w = w0 + row;
+            uint4 rv = make_uint4(0u, 0u, 0u, 0u);
+            if (w < n) {
+                const LearnedKey k = keys[w];
+                rv = philox(16u * k.j + (uint32_t)q, round_t, k.sim, 4u, k.key0, k.key1);
+            }
+            uint32_t* d = draws + row * 64 + 4 * q;
+            d[0] = rv.x; d[1] = rv.y; d[2] = rv.z; d[3] = rv.w;
+        }
     }
     // weights -> B fragments (registers)
     uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[5][2];
@@ -153,89 +177,113 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
     float lq_acc = 0.0f;
     __syncwarp();
 
-    for (int p = 0; p < kNPos; ++p) {
-        const int r = p / kS, c = p - r * kS, slot = p % kSlots;
-        // ---- layer 1: features (mask A interior taps + ring taps) ----
-        uint32_t a[4];
-        {
-            const int8_t* s = sp + g * kNPos;
-            float f[4];
+    uint32_t hprev[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};   // layer outputs at the previous column
+    float xprev = 0.0f;                                          // window g's spin at the previous column
+    for (int r = 0; r < kS; ++r) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int yy = r + fdy[e], xx = c + fdx[e];
-                float v = 0.0f;
-                if (fkind[e] != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
-                    const bool in = interior(yy, xx);
-                    if ((fkind[e] == 0) == in) v = (float)s[yy * kS + xx];
+        for (int c = 0; c < kS; ++c) {
+            const int p = r * kS + c, slot = p % kSlots;
+            // ---- layer 1: features (mask A interior taps + ring taps) ----
+            uint32_t a[4];
+            {
+                const int8_t* s = sp + g * kNPos;
+                float f[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int yy = r + fdy[e], xx = c + fdx[e];
+                    float v = 0.0f;
+                    if (fkind[e] != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
+                        const bool in = interior(yy, xx);
+                        if ((fkind[e] == 0) == in) {
+                            // the left neighbour in the current row is the spin just decided
+                            v = (fdy[e] == 0 && fkind[e] == 0) ? xprev : (float)s[yy * kS + xx];
+                        }
+                    }
+                    f[e] = v;
                 }
-                f[e] = v;
+                a[0] = pack_bf16(f[0], f[1]);
+                a[1] = 0u;
+                a[2] = pack_bf16(f[2], f[3]);
+                a[3] = 0u;
             }
-            a[0] = pack_bf16(f[0], f[1]);
-            a[1] = 0u;
-            a[2] = pack_bf16(f[2], f[3]);
-            a[3] = 0u;
-        }
+            uint32_t hcur[3][2];
 #pragma unroll
-        for (int layer = 0; layer < 3; ++layer) {
-            float d[2][2][4] = {};
-            if (layer == 0) {
-                mma16816(d[0][0], a, bw1[0]);
-                mma16816(d[0][1], a, bw1[1]);
-            } else {
+            for (int layer = 0; layer < 3; ++layer) {
+                float d[5][2][4] = {};   // one accumulator per tap: every mma of a layer is independent
+                if (layer == 0) {
+                    mma16816(d[0][0], a, bw1[0]);
+                    mma16816(d[0][1], a, bw1[1]);
+                } else {
 #pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
-                    if (yy < 0 || xx < 0 || xx >= kS) continue;
-                    const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
-                    const __nv_bfloat16* h0 = H(layer - 1, sl, g);
-                    uint32_t at[4];
+                    for (int t = 0; t < 5; ++t) {
+                        const int dy = (t < 3) ? -1 : 0, dx = (t < 3) ? t - 1 : (t == 3 ? -1 : 0);
+                        const int yy = r + dy, xx = c + dx;
+                        if (yy < 0 || xx < 0 || xx >= kS) continue;
+                        uint32_t at[4];
+                        if (t < 3) {            // previous row: from the ring
+                            const int sl = (p + dy * kS + dx + kSlots) % kSlots;
+                            const __nv_bfloat16* h0 = H(layer - 1, sl, g);
+                            at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
+                            at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
+                        } else if (t == 3) {    // previous column: registers
+                            at[0] = hprev[layer - 1][0];
+                            at[2] = hprev[layer - 1][1];
+                        } else {                // this position: registers
+                            at[0] = hcur[layer - 1][0];
+                            at[2] = hcur[layer - 1][1];
+                        }
+                        at[1] = 0u;
+                        at[3] = 0u;
+                        if (layer == 1) { mma16816(d[t][0], at, bw2[t][0]); mma16816(d[t][1], at, bw2[t][1]); }
+                        else { mma16816(d[t][0], at, bw3[t][0]); mma16816(d[t][1], at, bw3[t][1]); }
+                    }
+                }
+                // bias, relu, bf16: the A fragment of the next layer
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const float s0 = ((d[0][nt][0] + d[1][nt][0]) + (d[2][nt][0] + d[3][nt][0])) + d[4][nt][0];
+                    const float s1 = ((d[0][nt][1] + d[1][nt][1]) + (d[2][nt][1] + d[3][nt][1])) + d[4][nt][1];
+                    const uint32_t v0 = pack_bf16(fmaxf(s0 + bias[layer][nt][0], 0.f),
+                                                  fmaxf(s1 + bias[layer][nt][1], 0.f));
+                    hcur[layer][nt] = v0;
+                    *reinterpret_cast<uint32_t*>(H(layer, slot, g) + nt * 8 + 2 * tq) = v0;
+                    if (h_out && w0 + g < n)
+                        *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g) * kNPos + p) * kC +
+                                                     nt * 8 + 2 * tq) = v0;
+                }
+            }
+            // ---- layer 4: the logit ----
+            float d4[5][4] = {};
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                const int dy = (t < 3) ? -1 : 0, dx = (t < 3) ? t - 1 : (t == 3 ? -1 : 0);
+                const int yy = r + dy, xx = c + dx;
+                if (yy < 0 || xx < 0 || xx >= kS) continue;
+                uint32_t at[4];
+                if (t < 3) {
+                    const int sl = (p + dy * kS + dx + kSlots) % kSlots;
+                    const __nv_bfloat16* h0 = H(2, sl, g);
                     at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
-                    at[1] = 0u;
                     at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
-                    at[3] = 0u;
-                    if (layer == 1) { mma16816(d[t & 1][0], at, bw2[t][0]); mma16816(d[t & 1][1], at, bw2[t][1]); }
-                    else { mma16816(d[t & 1][0], at, bw3[t][0]); mma16816(d[t & 1][1], at, bw3[t][1]); }
+                } else if (t == 3) {
+                    at[0] = hprev[2][0];
+                    at[2] = hprev[2][1];
+                } else {
+                    at[0] = hcur[2][0];
+                    at[2] = hcur[2][1];
                 }
+                at[1] = 0u;
+                at[3] = 0u;
+                mma16816(d4[t], at, bw4[t]);
             }
-            // bias, relu, bf16 into the ring (and the activation output)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int co = nt * 8 + 2 * tq;
-                const uint32_t v0 = pack_bf16(fmaxf((d[0][nt][0] + d[1][nt][0]) + bias[layer][nt][0], 0.f),
-                                              fmaxf((d[0][nt][1] + d[1][nt][1]) + bias[layer][nt][1], 0.f));
-                *reinterpret_cast<uint32_t*>(H(layer, slot, g) + co) = v0;
-                if (h_out && w0 + g < n)
-                    *reinterpret_cast<uint32_t*>(h_out + (((size_t)layer * n + w0 + g) * kNPos + p) * kC + co) = v0;
-            }
-            __syncwarp();
-        }
-        // ---- layer 4: the logit ----
-        float d4[2][4] = {};
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-            const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
-            if (yy < 0 || xx < 0 || xx >= kS) continue;
-            const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
-            const __nv_bfloat16* h0 = H(2, sl, g);
-            uint32_t at[4];
-            at[0] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq);
-            at[1] = 0u;
-            at[2] = *reinterpret_cast<const uint32_t*>(h0 + 2 * tq + 8);
-            at[3] = 0u;
-            mma16816(d4[t & 1], at, bw4[t]);
-        }
-        if (tq == 0) {   // column 0 of the C fragment, row g = window w0 + g
-            const int w = w0 + g;
-            const float z = (d4[0][0] + d4[1][0]) + b4;
-            if (w < n) {
-                if (z_out) z_out[(size_t)w * kNPos + p] = z;
-                if (interior(r, c)) {
-                    int8_t x = sp[g * kNPos + p];
+            const float z = (((d4[0][0] + d4[1][0]) + (d4[2][0] + d4[3][0])) + d4[4][0]) + b4;   // lanes tq == 0
+            float xs = 0.0f;
+            if (interior(r, c)) {
+                const int w = w0 + g;
+                int8_t x = sp[g * kNPos + p];
+                if (tq == 0 && w < n) {
                     if (MODE == 1) {
-                        const LearnedKey k = keys[w];
-                        const int i = (r - 1) * kP + (c - 1);
-                        const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
-                        const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
+                        const uint32_t u = draws[g * 64 + (r - 1) * kP + (c - 1)];
                         const float sg = 1.0f / (1.0f + expf(-z));
                         const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
                         x = (u < thr) ? (int8_t)1 : (int8_t)-1;
@@ -243,12 +291,19 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
                     }
                     lq_acc += log_sigmoid((float)x * z);
                 }
+                if (MODE == 1) x = (int8_t)__shfl_sync(0xffffffffu, (int)x, lane & ~3);
+                xs = (float)x;
             }
+            if (tq == 0 && w0 + g < n && z_out) z_out[(size_t)(w0 + g) * kNPos + p] = z;
+#pragma unroll
+            for (int layer = 0; layer < 3; ++layer) { hprev[layer][0] = hcur[layer][0]; hprev[layer][1] = hcur[layer][1]; }
+            xprev = xs;
+            __syncwarp();
         }
-        __syncwarp();
     }
     if (tq == 0 && w0 + g < n) lq[w0 + g] = lq_acc;
     if (MODE == 1) {
+        __syncwarp();
         for (int i = lane; i < kWin * kNPos; i += 32) {
             const int row = i / kNPos;
             if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];

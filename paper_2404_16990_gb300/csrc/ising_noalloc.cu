@@ -118,7 +118,9 @@ extern "C" int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls
         const uint32_t tw = std::min<uint32_t>(s.groups, (uint32_t)threads);
         const uint32_t th = (uint32_t)threads / tw;
         const uint32_t tiles_x = (s.groups + tw - 1) / tw;
-        const uint32_t tiles_y = (L + th * rows - 1) / (th * rows);
+        const uint32_t Rl = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)rows, L / th));
+        s.rows = Rl;
+        const uint32_t tiles_y = (L + th * Rl - 1) / (th * Rl);
         s.strips = tiles_y;
         s.item_begin = tiles;
         tiles += (uint64_t)tiles_x * tiles_y;
@@ -147,7 +149,7 @@ extern "C" int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls
     const int occ = stream_occupancy(V, threads);
     if (occ <= 0) return set_last_error(ISING_ECUDA, "streaming kernel occupancy query failed");
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)device_sm_count() * occ);
-    e = launch_stream_sweeps(st, n_lat, tiles, V, rows, threads, grid, n, stream);
+    e = launch_stream_sweeps(st, n_lat, tiles, V, threads, grid, n, stream);
     if (e != cudaSuccess) return set_last_error(ISING_ECUDA, cudaGetErrorString(e));
     return ISING_OK;
 }

@@ -30,6 +30,7 @@ ISING_INIT_COLD = 1
 ISING_PLAN_AUTO = 0
 ISING_PLAN_RESIDENT = 1
 ISING_PLAN_STREAM = 2
+ISING_PLAN_PERSIST = 3
 ISING_MIN_L = 64
 ISING_MAX_L = 65536
 

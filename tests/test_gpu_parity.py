@@ -327,3 +327,30 @@ def test_autotune_keeps_state_and_bits(tmp_path, monkeypatch):
     sim2 = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds)
     assert sim2.autotune(probe_sweeps=3, force=False) == 0.0      # taken from the cache
     assert ising.ising_get_plan(sim2.h)["plan"] == plan["plan"]
+
+
+@pytest.mark.parametrize("Ls,V,R", [((2048,), 2, 4), ((64, 128, 192, 256, 1024), 1, 3), ((256,) * 12, 4, 2)])
+def test_persistent_streaming_kernel_bit_exact(Ls, V, R):
+    """All sweeps of a call in one cooperative launch (grid barrier between
+    half-sweeps), plain and through a CUDA graph."""
+    import torch
+    wl = workloads.random_batch(len(Ls), Ls=Ls, seed=len(Ls) + V)
+    n = 9
+    s = torch.cuda.Stream()
+    sims = []
+    for graph in (False, True):
+        sim = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=n, stream=s)
+        sim.set_plan(ising.ISING_PLAN_PERSIST, words_per_thread=V, rows_per_item=R)
+        sim.set_graph(graph)
+        sim.sweep(4)
+        sim.sweep(n - 4)
+        sims.append(sim)
+        assert ising.ising_kernel_launches(sim.h) == 2   # one launch per call
+    refs = [oracle.init(L, sd, i) for i, (L, sd) in enumerate(zip(wl.Ls, wl.seeds))]
+    Eo, Mo = oracle.sweeps_batch(refs, wl.temps, wl.seeds, list(range(len(refs))), 0, n, NT)
+    for sim in sims:
+        Eg, Mg = sim.trace(n)
+        assert np.array_equal(Eg, Eo) and np.array_equal(Mg, Mo)
+        for i in range(len(refs)):
+            assert np.array_equal(sim.spins(i), refs[i])
+        assert sim.sweeps_done == n
