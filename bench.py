@@ -32,6 +32,10 @@ OPS_PER_SITE = 18.5   # algorithmic integer ops per site update (derivation in D
 SMS = 152
 INT_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# (workload, kernel, sites per launch) -> dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch, from the committed ncu summary
+# profiles/stream_half_kernel_L16384x6.md (full capture, launch 1)
+MEASURED_TRAFFIC = {("l16384", "stream_half_kernel", 3 * 16384 * 16384 // 2): 110_520_000}
 
 
 def parse():
@@ -44,7 +48,7 @@ def parse():
     ap.add_argument("--L", type=int, default=16384)
     ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754)")
     ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
-    ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream"], default="tuned",
+    ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream", "persist"], default="tuned",
                     help="batch754: force a plan instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -225,7 +229,7 @@ def ours(args):
             sims.append(s)
     if args.workload == "batch754" and args.plan != "tuned":
         code = {"auto": ising.ISING_PLAN_AUTO, "resident": ising.ISING_PLAN_RESIDENT,
-                "stream": ising.ISING_PLAN_STREAM}[args.plan]
+                "stream": ising.ISING_PLAN_STREAM, "persist": ising.ISING_PLAN_PERSIST}[args.plan]
         for s in sims:
             s.set_plan(code)
     for s in sims:
@@ -271,23 +275,27 @@ def ours(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(flips_per_step, ws, ms_per_step / 1e3)
 
-    # dominant kernel: for the 16384^2 workload the streaming half-sweep (2
-    # launches per sweep per handle); for the batch the persistent resident
-    # kernel (one launch per step); either way the algorithmic ops of the
-    # timed region over its duration
+    # dominant kernel, from the plan in use: streaming half-sweeps (two
+    # launches per sweep per handle), the cooperative persistent streaming
+    # kernel or the resident kernel (one launch per sweep call per handle);
+    # either way the algorithmic ops of the timed region over its duration
     plan = ising.ising_get_plan(sims[0].h)
-    if args.workload == "l16384":
-        n_launch = 2 * n_sw * len(sims) * args.steps
-        kname = "stream_half_kernel"
+    if plan["plan"] == ising.ISING_PLAN_RESIDENT:
+        kname, n_launch = "resident_kernel", len(sims) * args.steps
+    elif plan["plan"] == ising.ISING_PLAN_PERSIST:
+        kname, n_launch = "stream_persist_kernel", len(sims) * args.steps
     else:
-        n_launch = args.steps
-        kname = "resident_kernel" if plan["plan"] != ising.ISING_PLAN_STREAM else "stream_half_kernel"
-        if kname == "stream_half_kernel":
-            n_launch = 2 * n_sw * args.steps
+        kname, n_launch = "stream_half_kernel", 2 * n_sw * len(sims) * args.steps
     avg_launch_s = (sum(step_ms) / 1e3) / n_launch
     sites_per_launch = flips_per_step * args.steps / n_launch
     achieved = OPS_PER_SITE * sites_per_launch / avg_launch_s / 1e12
     peak = SMS * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    # DRAM bytes (read + write) per launch from the ncu capture of this kernel
+    # on this workload; null for any other kernel / workload pairing
+    traffic = None
+    cap = MEASURED_TRAFFIC.get((args.workload, kname, int(round(sites_per_launch))))
+    if cap is not None:
+        traffic = cap
 
     # end-to-end through the public API: host checkpoint in (pinned), sweeps,
     # E/M traces and observables out, every step
@@ -342,7 +350,7 @@ def ours(args):
             "data": "synthetic",
             "config": cfg,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": kname, "ops_per_site": OPS_PER_SITE,
                          "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": cpu,

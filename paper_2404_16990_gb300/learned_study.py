@@ -158,6 +158,33 @@ def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000
     return res
 
 
+def round_bench(rounds: int = 20, L: int = 256, replicas: int = 64, precision: int = 0, seed: int = 7) -> dict:
+    """Device time of learned rounds alone (no training: seeded initial net) on
+    `replicas` lattices of side L at T_c."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        sim = ising.IsingSim(L, [T_CRITICAL] * replicas, seed, stream=s)
+        sim.sweep(100)
+        net = ising.IsingNet(max_windows=replicas * (L // 16) ** 2, max_lattices=replicas, stream=s, max_batch=512)
+        net.set_params(default_params(1))
+        net.set_precision(precision)
+        sim.learned_round(net, 0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for r in range(rounds):
+            sim.learned_round(net, r + 1, sync=False)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / max(1, rounds)
+    out = {"round_ms": ms, "patches": replicas * (L // 16) ** 2, "precision": "fp8" if precision else "bf16",
+           "accepted_fraction": float(net.accepted(replicas).sum()) / (rounds * replicas * (L // 16) ** 2)}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--temps", type=float, nargs="*", default=[2.20, T_CRITICAL, 2.35])
@@ -167,7 +194,12 @@ def main():
     ap.add_argument("--snapshots", type=int, default=20000)
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--units", type=int, default=20000)
+    ap.add_argument("--round-bench", type=int, default=0, help="only time this many learned rounds")
+    ap.add_argument("--fp8", action="store_true", help="with --round-bench: FP8 inference")
     args = ap.parse_args()
+    if args.round_bench:
+        round_bench(args.round_bench, precision=1 if args.fp8 else 0)
+        return
     out = [run_temperature(T, L=args.L, replicas=args.replicas, burn=args.burn, n_snap=args.snapshots,
                            train_steps=args.train_steps, units=args.units) for T in args.temps]
     print(json.dumps({"learned_study": out}))
