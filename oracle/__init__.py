@@ -8,8 +8,9 @@ definitions in ``paper_2404_16990_gb300.workloads`` (which hold none of the
 method's arithmetic) serve both sides.
 
 The arithmetic lives in ``ising_oracle.c`` (plain C, one byte per spin, the
-definitions of Section 1 and Algorithm 5 written out site by site); this
-module compiles it with gcc and wraps it with ctypes and numpy.
+definitions of Section 1 and Algorithm 5 written out site by site) and
+``cluster_oracle.c`` (the Swendsen-Wang cluster step named in Section 1);
+this module compiles them with gcc and wraps them with ctypes and numpy.
 """
 from __future__ import annotations
 
@@ -22,19 +23,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
+_SOURCES = ("ising_oracle.c", "cluster_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ising_oracle.c into oracle/liboracle.so (gcc, OpenMP)."""
+    """Compile the oracle sources into oracle/liboracle.so (gcc, OpenMP)."""
+    srcs = [os.path.join(_HERE, f) for f in _SOURCES]
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in srcs)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+           "-Wall", "-Wextra", "-o", tmp, *srcs, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -88,6 +91,26 @@ def _load():
         lib.oracle_window_sweeps.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.oracle_sw_threshold.argtypes = [ctypes.c_double, u32p]
+        lib.oracle_sw_threshold.restype = ctypes.c_int
+        lib.oracle_sw_bonds.argtypes = [ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32, u8p]
+        lib.oracle_sw_bonds.restype = None
+        lib.oracle_sw_labels.argtypes = [ctypes.c_int, u8p, u32p]
+        lib.oracle_sw_labels.restype = ctypes.c_int64
+        lib.oracle_sw_step.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_uint32, u8p, u32p]
+        lib.oracle_sw_step.restype = ctypes.c_int
+        lib.oracle_sw_sweeps.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, i64p, i64p]
+        lib.oracle_sw_sweeps.restype = ctypes.c_int
+        lib.oracle_sw_sweeps_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(i8p), u32p,
+                                               ctypes.POINTER(ctypes.c_uint64), u32p,
+                                               ctypes.c_uint32, ctypes.c_int64, i64p, i64p,
+                                               ctypes.c_int]
+        lib.oracle_sw_sweeps_batch.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -203,6 +226,73 @@ def window_state(L: int, seed: int, s: int, cold: bool, T: float, y: int, x: int
     return int(win[r, r])
 
 
+# --- Swendsen-Wang cluster step (cluster_oracle.c) ---------------------------
+
+def sw_threshold(T: float) -> int:
+    """u32 bond threshold floor(2^32 (1 - exp(-2/T))), clamped to 2^32 - 1."""
+    thr = np.zeros(1, dtype=np.uint32)
+    if _load().oracle_sw_threshold(float(T), _ptr(thr, ctypes.c_uint32)) != 0:
+        raise ValueError(f"invalid temperature {T!r}")
+    return int(thr[0])
+
+
+def sw_bonds(sigma: np.ndarray, T: float, seed: int, s: int, t: int) -> np.ndarray:
+    """Active bonds of step t: uint8 [L, L], bit 0 = right bond, bit 1 = down."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    L = sigma.shape[0]
+    bonds = np.zeros((L, L), dtype=np.uint8)
+    _load().oracle_sw_bonds(L, _ptr(sigma, ctypes.c_int8), seed, t, s, sw_threshold(T),
+                            _ptr(bonds, ctypes.c_uint8))
+    return bonds
+
+
+def sw_labels(bonds: np.ndarray):
+    """(labels uint32 [L, L] = smallest site index of each site's cluster,
+    number of clusters)."""
+    bonds = np.ascontiguousarray(bonds, dtype=np.uint8)
+    L = bonds.shape[0]
+    lab = np.zeros((L, L), dtype=np.uint32)
+    n = int(_load().oracle_sw_labels(L, _ptr(bonds, ctypes.c_uint8), _ptr(lab, ctypes.c_uint32)))
+    if n < 0:
+        raise MemoryError("oracle_sw_labels: allocation failed")
+    return lab, n
+
+
+def sw_sweeps(sigma: np.ndarray, T: float, seed: int, s: int, t0: int, n: int):
+    """In place: n Swendsen-Wang steps with indices t0..t0+n-1.  Returns the
+    (E, M) traces."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    E = np.zeros(max(n, 0), dtype=np.int64)
+    M = np.zeros(max(n, 0), dtype=np.int64)
+    rc = _load().oracle_sw_sweeps(sigma.shape[0], _ptr(sigma, ctypes.c_int8), sw_threshold(T), seed, s,
+                                  t0, n, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64))
+    if rc != 0:
+        raise MemoryError("oracle_sw_sweeps: allocation failed")
+    return E, M
+
+
+def sw_sweeps_batch(sigmas, temps, seeds, sims, t0: int, n: int, n_threads: int = 1):
+    """In place over a list of int8 lattices.  Returns traces [n_lat, n]."""
+    n_lat = len(sigmas)
+    Ls = np.array([x.shape[0] for x in sigmas], dtype=np.int32)
+    thr = np.array([sw_threshold(T) for T in temps], dtype=np.uint32)
+    seeds_a = np.array([int(x) for x in seeds], dtype=np.uint64)
+    sims_a = np.array([int(x) for x in sims], dtype=np.uint32)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * max(n_lat, 1))()
+    for j, x in enumerate(sigmas):
+        assert x.dtype == np.int8 and x.flags.c_contiguous
+        ptrs[j] = _ptr(x, ctypes.c_int8)
+    E = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    M = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    failed = _load().oracle_sw_sweeps_batch(n_lat, _ptr(Ls, ctypes.c_int), ptrs, _ptr(thr, ctypes.c_uint32),
+                                            _ptr(seeds_a, ctypes.c_uint64), _ptr(sims_a, ctypes.c_uint32),
+                                            t0, n, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64),
+                                            max(1, n_threads))
+    if failed:
+        raise MemoryError("oracle_sw_sweeps_batch: allocation failed")
+    return E, M
+
+
 class use_library:
     """Context manager: route every wrapper above through another build of the
     oracle source (used by the tests that plant mistakes in a copy of
@@ -243,17 +333,23 @@ def _load_no_build():
         globals()["build"] = saved_build
 
 
-def compile_variant(src_text: str, out_dir: str, name: str) -> str:
-    """Compile a (modified) copy of the oracle source into out_dir/name.so."""
-    src = os.path.join(out_dir, name + ".c")
+def compile_variant(src_text: str, out_dir: str, name: str, which: str = "ising_oracle.c") -> str:
+    """Compile the oracle with a (modified) copy of source file `which` and
+    the other sources unchanged into out_dir/name.so."""
+    assert which in _SOURCES
+    srcs = []
+    for f in _SOURCES:
+        path = os.path.join(out_dir, f"{name}_{f}")
+        with open(path, "w") as fh:
+            fh.write(src_text if f == which else source_text(f))
+        srcs.append(path)
     so = os.path.join(out_dir, name + ".so")
-    with open(src, "w") as f:
-        f.write(src_text)
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                           "-o", so, src, "-lm"])
+                           "-o", so, *srcs, "-lm"])
     return so
 
 
-def source_text() -> str:
-    with open(_SRC) as f:
+def source_text(which: str = "ising_oracle.c") -> str:
+    assert which in _SOURCES
+    with open(os.path.join(_HERE, which)) as f:
         return f.read()

@@ -57,3 +57,54 @@ def test_pins_catch_planted_mistake(name, tmp_path):
 def test_unmodified_source_passes_same_checks(tmp_path):
     so = oracle.compile_variant(oracle.source_text(), str(tmp_path), "oracle_clean")
     assert _caught(so) == []
+
+
+# --------------------------------------------------------------------------
+# The same for the Swendsen-Wang oracle (cluster_oracle.c).
+# --------------------------------------------------------------------------
+import test_cluster_oracle as swpins  # noqa: E402
+
+SW_MUTATIONS = {
+    "sw_bond_probability": ("double p = -expm1(-2.0 / T);", "double p = -expm1(-1.0 / T);"),
+    "sw_down_bond_dropped": ("if (me == down && r_down < thr) b |= 2u;", ""),
+    "sw_bond_unequal_spins": ("if (me == right && r_right < thr) b |= 1u;",
+                              "if (me != right && r_right < thr) b |= 1u;"),
+    "sw_coin_per_site": ("oracle_site_random(seed, root, t, s, ORC_SW_PHASE_COIN)",
+                         "oracle_site_random(seed, (uint32_t)p, t, s, ORC_SW_PHASE_COIN)"),
+    "sw_left_neighbour_missed": ("if (bonds[left] & 1u) nb[k++] = left;", ""),
+    "sw_same_lane_both_bonds": ("uint32_t r_down = out[2u * (p & 1u) + 1u];",
+                                "uint32_t r_down = out[2u * (p & 1u)];"),
+}
+
+
+def _caught_sw(variant_so) -> list:
+    caught = []
+    with oracle.use_library(variant_so):
+        checks = [
+            ("threshold", swpins.test_sw_threshold_exact),
+            ("bonds", lambda: swpins.test_bonds_between_equal_spins_at_rate_p(exact.T_C)),
+            ("lanes", swpins.test_bonds_right_and_down_draws_are_distinct_lanes),
+            ("labels", lambda: swpins.test_labels_match_connected_components(16, 0.45)),
+            ("chi2_4x4", lambda: swpins.test_sw_4x4_joint_distribution_matches_enumeration(exact.T_C)),
+        ]
+        for name, fn in checks:
+            try:
+                fn()
+            except AssertionError:
+                caught.append(name)
+    return caught
+
+
+@pytest.mark.parametrize("name", sorted(SW_MUTATIONS))
+def test_sw_pins_catch_planted_mistake(name, tmp_path):
+    old, new = SW_MUTATIONS[name]
+    src = oracle.source_text("cluster_oracle.c")
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    so = oracle.compile_variant(src.replace(old, new), str(tmp_path), "sw_" + name, which="cluster_oracle.c")
+    assert _caught_sw(so), f"no pin caught the planted mistake {name}"
+
+
+def test_sw_unmodified_source_passes_same_checks(tmp_path):
+    so = oracle.compile_variant(oracle.source_text("cluster_oracle.c"), str(tmp_path), "sw_clean",
+                                which="cluster_oracle.c")
+    assert _caught_sw(so) == []
