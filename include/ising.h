@@ -367,6 +367,53 @@ int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls, const dou
                         const uint64_t* seeds, int64_t t0, int64_t n, int64_t* dev_EM,
                         void* cuda_stream);
 
+/* ---- Swendsen-Wang cluster step -----------------------------------------
+ * Section 1 names cluster algorithms (Swendsen-Wang, Wolff) as the cure for
+ * the critical slowing down of single-site Metropolis.  One step (Swendsen
+ * and Wang, PRL 58, 86 (1987)), J = 1, h = 0: every nearest-neighbour pair of
+ * equal spins gets an active bond with probability p = 1 - exp(-2/T); the
+ * clusters are the connected components of the active bonds; each cluster
+ * flips with probability 1/2.  Draws (Philox4x32-10 keyed by the lattice's
+ * seed, counter (q, t, s, phase), t = the step's index in the handle's sweep
+ * counter, s = simulation index):
+ *   bonds, phase 7: site p = y*L + x owns the bonds to (x+1, y) and (x, y+1)
+ *     (indices mod L); q = p >> 1, lane 2*(p & 1) is the right bond's draw,
+ *     lane 2*(p & 1) + 1 the down bond's; a bond between equal spins is
+ *     active iff its draw is below floor(2^32 p) (at most 2^32 - 1);
+ *   coins, phase 8: a cluster is named by its smallest site index r0 (its
+ *     root) and flips iff the top bit of lane r0 & 3 of block r0 >> 2 is 1.
+ * Steps and Metropolis sweeps share the sweep counter and may be mixed. */
+#define ISING_SW_MAX_L 32768
+
+/* Bytes of device scratch one cluster step of this handle needs: the
+ * per-lattice table, 16 bytes per 64 x 32 tile, one coin bit and one 32-bit
+ * label per site (about 4.14 bytes per site).  ISING_EINVAL if a lattice has
+ * L > ISING_SW_MAX_L. */
+int ising_sw_scratch_bytes(ising_t h, size_t* bytes);
+
+/* The bond thresholds floor(2^32 (1 - exp(-2/T))) of every lattice (host
+ * array thr[n_sims], caller-owned). */
+int ising_sw_get_thresholds(ising_t h, uint32_t* thr);
+
+/* Advance every lattice by n >= 0 Swendsen-Wang steps.  dev_scratch: device
+ * memory (256-byte aligned, caller-owned, contents need not be kept between
+ * calls) of scratch_bytes >= ising_sw_scratch_bytes; it must not be used by
+ * anything else while the steps run.  Asynchronous on the handle's stream;
+ * after each step E and M are recorded exactly as after a sweep (current
+ * values, trace ring, FP64 moments if measuring) and the sweep counter
+ * advances by one.  Graph replay (ising_set_graph) captures n steps per
+ * (n, scratch) pair.  ISING_ENOMEM if the scratch is too small; a union-find
+ * walk that runs past its bound (impossible for a consistent label array)
+ * makes the next synchronising call return ISING_ETIMEOUT. */
+int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes);
+
+/* Cluster labels of lattice `sim` for the step the handle would take next
+ * (its current sweep counter), without taking it: host_labels[L*L]
+ * (caller-owned) receives, for every site p = y*L + x, the smallest site
+ * index of its cluster.  Synchronises the stream.  The spins and the sweep
+ * counter are unchanged. */
+int ising_sw_labels(ising_t h, int sim, void* dev_scratch, size_t scratch_bytes, uint32_t* host_labels);
+
 /* Free the handle (not the workspace).  Synchronises its stream. */
 void ising_destroy(ising_t h);
 

@@ -139,6 +139,10 @@ struct ising_handle {
     int stream_grid = 0;
     int sms = 0;
     int64_t launches = 0;
+    // Swendsen-Wang: per-lattice table (built once) and its upload target
+    std::vector<SwLat> sw_table;
+    uint64_t sw_tiles = 0, sw_sites = 0;
+    std::map<std::pair<int64_t, const void*>, cudaGraphExec_t> sw_graphs;
 };
 
 namespace {
@@ -146,6 +150,8 @@ namespace {
 void drop_graphs(ising_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
+    for (auto& kv : h->sw_graphs) cudaGraphExecDestroy(kv.second);
+    h->sw_graphs.clear();
 }
 
 int check_device_error(ising_handle* h) {
@@ -153,8 +159,10 @@ int check_device_error(ising_handle* h) {
     CUDA_TRY(cudaMemcpyAsync(&err, &h->st.ctl->error, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
              "read error flag");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    if (err == 3)
+        return fail(ISING_ETIMEOUT, "a bounded union-find walk of the cluster step ran out (flag %d)", err);
     if (err != 0)
-        return fail(ISING_ETIMEOUT, "a bounded device wait of the resident kernel ran out (flag %d)", err);
+        return fail(ISING_ETIMEOUT, "a bounded device wait of the sweep kernels ran out (flag %d)", err);
     return ISING_OK;
 }
 
@@ -926,6 +934,172 @@ void ising_destroy(ising_t h) {
     cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     delete h;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Swendsen-Wang cluster step (kernels in ising_cluster.cu)
+// ===========================================================================
+namespace {
+
+constexpr int kSwTileSites = 64 * 32;
+constexpr int kSwKernels = 7;   // local, merge, flatten, flip, observables (2), record
+
+struct SwLayout {
+    size_t lat = 0, edges = 0, coins = 0, label = 0, total = 0;
+};
+
+// bond threshold floor(2^32 (1 - exp(-2/T))), at most 2^32 - 1
+uint32_t sw_threshold_u32(double T) {
+    const double v = std::ldexp(-std::expm1(-2.0 / T), 32);
+    if (v >= 4294967296.0) return 0xFFFFFFFFu;
+    return (uint32_t)std::floor(v);
+}
+
+int sw_build_table(ising_handle* h) {
+    if (!h->sw_table.empty() || h->n == 0) return ISING_OK;
+    uint64_t tiles = 0, sites = 0;
+    std::vector<SwLat> tab((size_t)h->n);
+    for (int i = 0; i < h->n; ++i) {
+        if (h->L[i] > ISING_SW_MAX_L)
+            return fail(ISING_EINVAL, "lattice %d: the cluster step takes L <= %d (L=%d)", i, ISING_SW_MAX_L, h->L[i]);
+        SwLat d{};
+        d.word_off = h->layout.word_off[i];
+        d.site_off = sites;
+        d.L = (uint32_t)h->L[i];
+        d.wn = (uint32_t)(h->L[i] / 64);
+        d.sim = (uint32_t)i;
+        d.key0 = (uint32_t)(h->seed[i] & 0xFFFFFFFFull);
+        d.key1 = (uint32_t)(h->seed[i] >> 32);
+        d.thr = sw_threshold_u32(h->T[i]);
+        d.tile_begin = (uint32_t)tiles;
+        tab[i] = d;
+        const uint64_t n2 = (uint64_t)h->L[i] * (uint64_t)h->L[i];
+        sites += n2;
+        tiles += n2 / kSwTileSites;
+        if (tiles >= 0x7FFFFFFFull) return fail(ISING_EINVAL, "too many sites for one cluster step");
+    }
+    h->sw_tiles = tiles;
+    h->sw_sites = sites;
+    h->sw_table = std::move(tab);
+    return ISING_OK;
+}
+
+SwLayout sw_layout(const ising_handle* h) {
+    SwLayout l;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    l.lat = take((size_t)h->n * sizeof(SwLat));
+    l.edges = take((size_t)h->sw_tiles * sizeof(uint4));
+    l.coins = take((size_t)(h->sw_sites / 32) * sizeof(uint32_t));
+    l.label = take((size_t)h->sw_sites * sizeof(uint32_t));
+    l.total = off;
+    return l;
+}
+
+// Validate the scratch, upload the table, fill sw.
+int sw_prepare(ising_handle* h, void* scratch, size_t bytes, SwState* sw) {
+    int rc = sw_build_table(h);
+    if (rc != ISING_OK) return rc;
+    const SwLayout l = sw_layout(h);
+    if (!scratch) return fail(ISING_EINVAL, "scratch is NULL");
+    if (((uintptr_t)scratch) % kAlign != 0) return fail(ISING_EINVAL, "scratch must be 256-byte aligned");
+    if (bytes < l.total) return fail(ISING_ENOMEM, "cluster scratch too small: %zu bytes given, %zu needed", bytes, l.total);
+    char* base = (char*)scratch;
+    // the table is tiny: upload it on every call, so that a scratch that was
+    // freed and reallocated at the same address never runs with a stale one
+    // (the host copy lives as long as the handle)
+    CUDA_TRY(cudaMemcpyAsync(base + l.lat, h->sw_table.data(), h->sw_table.size() * sizeof(SwLat),
+                             cudaMemcpyHostToDevice, h->stream), "upload cluster table");
+    sw->lat = (const SwLat*)(base + l.lat);
+    sw->n = h->n;
+    sw->total_tiles = (uint32_t)h->sw_tiles;
+    sw->edges = (uint4*)(base + l.edges);
+    sw->coins = (uint32_t*)(base + l.coins);
+    sw->label = (uint32_t*)(base + l.label);
+    return ISING_OK;
+}
+
+int enqueue_sw(ising_handle* h, const SwState& sw, int64_t n) {
+    const uint32_t* list = (const uint32_t*)(h->ws + h->layout.list);
+    for (int64_t i = 0; i < n; ++i) {
+        CUDA_TRY(launch_sw_clusters(h->st, sw, h->stream), "cluster labelling");
+        CUDA_TRY(launch_sw_flip(h->st, sw, h->stream), "cluster flip");
+        CUDA_TRY(launch_observables(h->st, h->n, list, h->n, h->stream), "observables");
+        CUDA_TRY(launch_sw_record(h->st, h->n, h->stream), "record");
+    }
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_sw_scratch_bytes(ising_t h, size_t* bytes) {
+    if (!h || !bytes) return fail(ISING_EINVAL, "handle or bytes is NULL");
+    int rc = sw_build_table(h);
+    if (rc != ISING_OK) return rc;
+    *bytes = sw_layout(h).total;
+    return ISING_OK;
+}
+
+int ising_sw_get_thresholds(ising_t h, uint32_t* thr) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (h->n > 0 && !thr) return fail(ISING_EINVAL, "thr is NULL");
+    for (int i = 0; i < h->n; ++i) thr[i] = sw_threshold_u32(h->T[i]);
+    return ISING_OK;
+}
+
+int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
+    if (h->n == 0) return ISING_OK;
+    if (h->t + n > (int64_t)0xFFFFFFFFll)
+        return fail(ISING_EINVAL, "sweep counter would pass 2^32 (Philox counter word 1)");
+    SwState sw{};
+    int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
+    if (rc != ISING_OK || n == 0) return rc;
+    if (h->graph) {
+        if (h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");
+        const auto key = std::make_pair(n, (const void*)dev_scratch);
+        auto it = h->sw_graphs.find(key);
+        if (it == h->sw_graphs.end()) {
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            rc = enqueue_sw(h, sw, n);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (rc != ISING_OK) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            it = h->sw_graphs.emplace(key, ex).first;
+        }
+        CUDA_TRY(cudaGraphLaunch(it->second, h->stream), "graph launch");
+    } else {
+        rc = enqueue_sw(h, sw, n);
+        if (rc != ISING_OK) return rc;
+    }
+    h->t += n;
+    h->launches += kSwKernels * n;
+    return ISING_OK;
+}
+
+int ising_sw_labels(ising_t h, int sim, void* dev_scratch, size_t scratch_bytes, uint32_t* host_labels) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (sim < 0 || sim >= h->n) return fail(ISING_EINVAL, "sim %d out of range", sim);
+    if (!host_labels) return fail(ISING_EINVAL, "host_labels is NULL");
+    SwState sw{};
+    int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
+    if (rc != ISING_OK) return rc;
+    CUDA_TRY(launch_sw_clusters(h->st, sw, h->stream), "cluster labelling");
+    h->launches += 3;
+    const SwLat& d = h->sw_table[sim];
+    CUDA_TRY(cudaMemcpyAsync(host_labels, sw.label + d.site_off, (size_t)d.L * d.L * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, h->stream), "copy labels");
+    return check_device_error(h);
 }
 
 }  // extern "C"

@@ -1,0 +1,345 @@
+// ising_cluster.cu -- sm_103a kernels of the Swendsen-Wang cluster step.
+//
+// The paper names cluster algorithms (Swendsen-Wang, Wolff) as the remedy for
+// the critical slowing down of single-site Metropolis (Section 1).  One
+// Swendsen-Wang step (Swendsen and Wang 1987), J = 1, h = 0, periodic L x L:
+//   1. every nearest-neighbour pair of equal spins gets an active bond with
+//      probability 1 - exp(-2/T);
+//   2. clusters = connected components of the active bonds;
+//   3. each cluster flips with probability 1/2.
+// Draws: Philox4x32-10 keyed by the lattice seed, counter (q, t, s, phase).
+// Bonds (phase 7): site p = y*L + x owns its right and down bonds, q = p >> 1,
+// lane 2*(p & 1) for the right bond and 2*(p & 1) + 1 for the down bond; a
+// bond between equal spins is active iff its draw is below the threshold.
+// Coins (phase 8): a cluster is named by its smallest site index r0 and flips
+// iff the top bit of lane r0 & 3 of block r0 >> 2 is set.  The partition and
+// its minimum-index roots are unique, so the step is bit-reproducible
+// whatever the labelling order.
+//
+// Labelling is a lock-free union-find whose links always point from a larger
+// to a smaller index (atomicMin on the larger root), so that a component's
+// final root is its smallest index:
+//   sw_local_kernel   one CTA per 64 x 32 tile: spins from the packed words,
+//                     bonds, union-find over the tile's internal bonds in
+//                     shared memory, global labels, the tile's edge bonds;
+//   sw_merge_kernel   unions over the bonds that cross tile edges (global);
+//   sw_flatten_kernel every site points at its root; coins of the roots;
+//   sw_flip_kernel    both colour words of (y, k) flipped by their roots' coins.
+// Every pointer walk and union retry is bounded; running past a bound (which
+// the strictly decreasing links make impossible for a consistent array) sets
+// the error word and leaves the labels in range.
+#include "ising_internal.h"
+#include "ising_device.cuh"
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ising {
+namespace {
+
+constexpr int kTileW = 64, kTileH = 32, kTileSites = kTileW * kTileH;
+constexpr int kWordsPerTile = kTileSites / 32;     // flatten: one thread per 32 sites
+constexpr int kPairsPerTile = kTileSites / 64;     // flip: one thread per 64 sites
+constexpr int kEdgeSites = kTileH + kTileW;        // merge: right edge rows + bottom edge columns
+constexpr uint32_t kPhaseBond = 7u, kPhaseCoin = 8u;
+constexpr int kMaxChain = 1 << 26;                 // bound on one parent-pointer walk
+constexpr int kMaxRetry = 1 << 22;                 // bound on the retries of one union
+constexpr int kErrUnionBound = 3;                  // error word value
+
+// Lattice of a tile: the last lattice with tile_begin <= tile.
+__device__ __forceinline__ int lattice_of_tile(const SwLat* lat, int n, uint32_t tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (lat[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The 32 bits of v moved to the even bit positions of a 64-bit word.
+__device__ __forceinline__ uint64_t spread_even(uint32_t v) {
+    uint64_t x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+
+// Sites x in [64k, 64k + 64) of row y in natural order (bit i <-> x = 64k + i):
+// colour c holds x = 2(32k + b) + ((y + c) & 1), so even x come from colour
+// y & 1 and odd x from the other one.
+__device__ __forceinline__ uint64_t natural_row(const uint32_t* base, uint32_t L, uint32_t wn, uint32_t y,
+                                                uint32_t k) {
+    const uint32_t ce = y & 1u;
+    const uint32_t we = base[((size_t)ce * L + y) * wn + k];
+    const uint32_t wo = base[((size_t)(ce ^ 1u) * L + y) * wn + k];
+    return spread_even(we) | (spread_even(wo) << 1);
+}
+
+// --- union-find in shared memory (one tile, indices < kTileSites) ---------
+__device__ __forceinline__ uint32_t find_tile(const volatile uint32_t* lab, uint32_t x) {
+    uint32_t p = lab[x];
+    for (int it = 0; it < kTileSites && p != x; ++it) {
+        x = p;
+        p = lab[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void unite_tile(uint32_t* lab, uint32_t a, uint32_t b) {
+    for (int it = 0; it < kTileSites; ++it) {
+        a = find_tile(lab, a);
+        b = find_tile(lab, b);
+        if (a == b) return;
+        if (a > b) { const uint32_t s = a; a = b; b = s; }
+        const uint32_t old = atomicMin(&lab[b], a);
+        if (old == b) return;     // b was a root and now hangs under a
+        b = old;                  // b had been linked meanwhile: merge a with its parent
+    }
+}
+
+// --- union-find in global memory (one lattice) ----------------------------
+// Returns the root, or ~0u if the walk ran past its bound.
+__device__ __forceinline__ uint32_t find_global(uint32_t* lab, uint32_t x) {
+    const volatile uint32_t* v = lab;
+    uint32_t p = v[x];
+    for (int it = 0; it < kMaxChain; ++it) {
+        if (p == x) return x;
+        const uint32_t gp = v[p];
+        if (gp != p) atomicMin(&lab[x], gp);   // path halving; links only ever decrease
+        x = p;
+        p = gp;
+    }
+    return ~0u;
+}
+
+__device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t b) {
+    for (int it = 0; it < kMaxRetry; ++it) {
+        a = find_global(lab, a);
+        b = find_global(lab, b);
+        if (a == ~0u || b == ~0u) return false;
+        if (a == b) return true;
+        if (a > b) { const uint32_t s = a; a = b; b = s; }
+        const uint32_t old = atomicMin(&lab[b], a);
+        if (old == b) return true;
+        b = old;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Bonds and tile-local labels.  256 threads: thread (ly, seg) handles the 8
+// sites x0 + 8 seg .. + 7 of row y0 + ly (4 Philox blocks).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sw_local_kernel(DevState st, SwState sw) {
+    __shared__ uint64_t s_row[kTileH + 1];
+    __shared__ uint32_t s_rbit[kTileH + 1];
+    __shared__ uint32_t s_lab[kTileSites];
+    __shared__ uint32_t s_edge_r;
+    __shared__ unsigned long long s_edge_d;
+    __shared__ int s_lat;
+
+    const uint32_t tile = blockIdx.x;
+    if (threadIdx.x == 0) {
+        s_lat = lattice_of_tile(sw.lat, sw.n, tile);
+        s_edge_r = 0u;
+        s_edge_d = 0ull;
+    }
+    for (int i = threadIdx.x; i < kTileSites; i += blockDim.x) s_lab[i] = (uint32_t)i;
+    __syncthreads();
+    const SwLat d = sw.lat[s_lat];
+    const uint32_t L = d.L, wn = d.wn;
+    const uint32_t local = tile - d.tile_begin;
+    const uint32_t tx = local % wn, ty = local / wn;     // L / 64 tiles per tile row
+    const uint32_t x0 = kTileW * tx, y0 = kTileH * ty;
+    const uint32_t* base = st.spins + d.word_off;
+    const uint32_t t = (uint32_t)st.ctl->t;
+
+    // rows y0 .. y0 + 32 (the last wraps at the lattice edge) and, for each,
+    // the site just right of the tile (x = 64 (tx + 1) mod L: even, colour y & 1)
+    if (threadIdx.x <= kTileH) {
+        uint32_t y = y0 + threadIdx.x;
+        if (y >= L) y -= L;
+        s_row[threadIdx.x] = natural_row(base, L, wn, y, tx);
+        const uint32_t kr = (tx + 1 == wn) ? 0u : tx + 1;
+        s_rbit[threadIdx.x] = base[((size_t)(y & 1u) * L + y) * wn + kr] & 1u;
+    }
+    __syncthreads();
+
+    const uint32_t ly = threadIdx.x >> 3, seg = threadIdx.x & 7u, lx0 = 8u * seg;
+    const uint64_t row = s_row[ly], below = s_row[ly + 1];
+    const uint64_t right = (row >> 1) | ((uint64_t)s_rbit[ly] << 63);
+    const uint32_t al_r = (uint32_t)(~(row ^ right) >> lx0) & 0xFFu;   // equal to the right neighbour
+    const uint32_t al_d = (uint32_t)(~(row ^ below) >> lx0) & 0xFFu;   // equal to the neighbour below
+    const uint32_t p0 = (y0 + ly) * L + x0 + lx0;                      // even
+    uint32_t b_r = 0, b_d = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        const uint4 r = philox((p0 >> 1) + j, t, d.sim, kPhaseBond, d.key0, d.key1);
+        b_r |= ((uint32_t)(r.x < d.thr) << (2 * j)) | ((uint32_t)(r.z < d.thr) << (2 * j + 1));
+        b_d |= ((uint32_t)(r.y < d.thr) << (2 * j)) | ((uint32_t)(r.w < d.thr) << (2 * j + 1));
+    }
+    b_r &= al_r;
+    b_d &= al_d;
+
+    const uint32_t i0 = ly * kTileW + lx0;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+        if (((b_r >> j) & 1u) && lx0 + j < kTileW - 1) unite_tile(s_lab, i0 + j, i0 + j + 1);
+        if (((b_d >> j) & 1u) && ly < kTileH - 1) unite_tile(s_lab, i0 + j, i0 + j + kTileW);
+    }
+    if (seg == 7u && ((b_r >> 7) & 1u)) atomicOr(&s_edge_r, 1u << ly);
+    if (ly == kTileH - 1 && b_d) atomicOr(&s_edge_d, (unsigned long long)b_d << lx0);
+    __syncthreads();
+
+    uint32_t out[8];
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+        const uint32_t r = find_tile(s_lab, i0 + j);
+        out[j] = (y0 + (r >> 6)) * L + x0 + (r & 63u);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(sw.label + d.site_off + p0);
+    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    if (threadIdx.x == 0)
+        sw.edges[tile] = make_uint4(s_edge_r, 0u, (uint32_t)s_edge_d, (uint32_t)(s_edge_d >> 32));
+}
+
+// ---------------------------------------------------------------------------
+// Unions over the bonds leaving each tile to the right and downwards.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sw_merge_kernel(DevState st, SwState sw) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t tile = gid / kEdgeSites;
+    if (tile >= sw.total_tiles) return;
+    const uint32_t e = (uint32_t)(gid - tile * kEdgeSites);
+    const uint4 ed = sw.edges[tile];
+    const bool on = (e < (uint32_t)kTileH) ? ((ed.x >> e) & 1u) != 0
+                                          : ((e - kTileH < 32u) ? ((ed.z >> (e - kTileH)) & 1u) != 0
+                                                                : ((ed.w >> (e - kTileH - 32u)) & 1u) != 0);
+    if (!on) return;
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)tile)];
+    const uint32_t L = d.L, wn = d.wn;
+    const uint32_t local = (uint32_t)tile - d.tile_begin;
+    const uint32_t x0 = kTileW * (local % wn), y0 = kTileH * (local / wn);
+    uint32_t a, b;
+    if (e < (uint32_t)kTileH) {
+        const uint32_t y = y0 + e, xr = (x0 + kTileW == L) ? 0u : x0 + kTileW;
+        a = y * L + x0 + kTileW - 1;
+        b = y * L + xr;
+    } else {
+        const uint32_t x = x0 + (e - kTileH), yb = (y0 + kTileH == L) ? 0u : y0 + kTileH;
+        a = (y0 + kTileH - 1) * L + x;
+        b = yb * L + x;
+    }
+    if (!unite_global(sw.label + d.site_off, a, b)) atomicExch(&st.ctl->error, kErrUnionBound);
+}
+
+// ---------------------------------------------------------------------------
+// Every site points at its root; roots draw their coins.  One thread per 32
+// consecutive sites (one coin word).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sw_flatten_kernel(DevState st, SwState sw) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)sw.total_tiles * kWordsPerTile) return;
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)(g / kWordsPerTile))];
+    const uint32_t w = (uint32_t)(g - (uint64_t)d.tile_begin * kWordsPerTile);   // word within the lattice
+    uint32_t* lab = sw.label + d.site_off;
+    const uint32_t t = (uint32_t)st.ctl->t;
+    uint32_t coin = 0;
+    bool failed = false;
+#pragma unroll 2
+    for (uint32_t j = 0; j < 32; j += 4) {
+        uint32_t roots = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i) {
+            const uint32_t p = 32u * w + j + i;
+            const uint32_t r = find_global(lab, p);
+            if (r == ~0u) { failed = true; continue; }
+            lab[p] = r;
+            if (r == p) roots |= 1u << i;
+        }
+        if (roots) {
+            const uint4 v = philox((32u * w + j) >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
+            const uint32_t c = ((v.x >> 31) & roots) | (((v.y >> 31) << 1) & roots) |
+                               (((v.z >> 31) << 2) & roots) | (((v.w >> 31) << 3) & roots);
+            coin |= c << j;
+        }
+    }
+    if (failed) atomicExch(&st.ctl->error, kErrUnionBound);
+    sw.coins[d.site_off / 32 + w] = coin;
+}
+
+// ---------------------------------------------------------------------------
+// Flip: both colour words of (y, k), i.e. the 64 sites x in [64k, 64k + 64).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sw_flip_kernel(DevState st, SwState sw) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)sw.total_tiles * kPairsPerTile) return;
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)(g / kPairsPerTile))];
+    const uint32_t i = (uint32_t)(g - (uint64_t)d.tile_begin * kPairsPerTile);
+    const uint32_t L = d.L, wn = d.wn;
+    const uint32_t y = i / wn, k = i - y * wn;
+    const uint32_t p0 = y * L + 64u * k;
+    const uint4* lab = reinterpret_cast<const uint4*>(sw.label + d.site_off + p0);
+    const uint32_t* coins = sw.coins + d.site_off / 32;
+    uint32_t m_even = 0, m_odd = 0;
+#pragma unroll 4
+    for (uint32_t q = 0; q < 16; ++q) {
+        const uint4 r = lab[q];
+        const uint32_t c0 = (coins[r.x >> 5] >> (r.x & 31u)) & 1u;
+        const uint32_t c1 = (coins[r.y >> 5] >> (r.y & 31u)) & 1u;
+        const uint32_t c2 = (coins[r.z >> 5] >> (r.z & 31u)) & 1u;
+        const uint32_t c3 = (coins[r.w >> 5] >> (r.w & 31u)) & 1u;
+        m_even |= (c0 << (2 * q)) | (c2 << (2 * q + 1));
+        m_odd |= (c1 << (2 * q)) | (c3 << (2 * q + 1));
+    }
+    uint32_t* base = st.spins + d.word_off;
+    const uint32_t ce = y & 1u;
+    base[((size_t)ce * L + y) * wn + k] ^= m_even;
+    base[((size_t)(ce ^ 1u) * L + y) * wn + k] ^= m_odd;
+}
+
+// E, M of the step (already in obs) into the trace and moments; then advance
+// the device sweep counter.  One block.
+__global__ void sw_record_kernel(DevState st, int n_lat) {
+    const unsigned long long t = st.ctl->t;
+    for (int lat = threadIdx.x; lat < n_lat; lat += blockDim.x)
+        record_em(st, (uint32_t)lat, st.lat[lat].L, st.obs[2 * lat], st.obs[2 * lat + 1], t);
+    __syncthreads();
+    if (threadIdx.x == 0) st.ctl->t = t + 1;
+}
+
+}  // namespace
+
+cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream) {
+    if (sw.n <= 0 || sw.total_tiles == 0) return cudaSuccess;
+    sw_local_kernel<<<sw.total_tiles, 256, 0, stream>>>(st, sw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t edge_threads = (uint64_t)sw.total_tiles * kEdgeSites;
+    sw_merge_kernel<<<(unsigned)((edge_threads + 255) / 256), 256, 0, stream>>>(st, sw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t words = (uint64_t)sw.total_tiles * kWordsPerTile;
+    sw_flatten_kernel<<<(unsigned)((words + 255) / 256), 256, 0, stream>>>(st, sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t stream) {
+    if (sw.n <= 0 || sw.total_tiles == 0) return cudaSuccess;
+    const uint64_t pairs = (uint64_t)sw.total_tiles * kPairsPerTile;
+    sw_flip_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, stream>>>(st, sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream) {
+    if (n_lat <= 0) return cudaSuccess;
+    sw_record_kernel<<<1, 256, 0, stream>>>(st, n_lat);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

@@ -1,8 +1,11 @@
-// ising_device.cuh -- device helpers shared by the sweep kernels and the
-// learned-proposal kernels: the Philox4x32-10 counter-based generator.
+// ising_device.cuh -- device helpers shared by the sweep kernels, the
+// cluster kernels and the learned-proposal kernels: the Philox4x32-10
+// counter-based generator and the per-sweep observable record.
 #pragma once
 
 #include <cstdint>
+
+#include "ising_internal.h"
 
 namespace ising {
 
@@ -31,6 +34,32 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
         c3 = lo_a;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+// Store E and M of lattice `lat` after sweep t: current values, the trace
+// ring slot t % cap, and (if measuring) the FP64 moments of m = M/N, e = E/N.
+__device__ __forceinline__ void record_em(const DevState& st, uint32_t lat, uint32_t L, long long E,
+                                          long long M, unsigned long long t) {
+    st.obs[2 * lat + 0] = E;
+    st.obs[2 * lat + 1] = M;
+    const long long cap = st.ctl->trace_cap;
+    if (cap > 0) {
+        const long long slot = (long long)(t % (unsigned long long)cap);
+        st.trace[((long long)lat * cap + slot) * 2 + 0] = E;
+        st.trace[((long long)lat * cap + slot) * 2 + 1] = M;
+    }
+    if (st.ctl->measure) {
+        const double inv = 1.0 / ((double)L * (double)L);
+        const double m = (double)M * inv, e = (double)E * inv;
+        const double m2 = m * m;
+        double* mo = st.mom + 6 * (size_t)lat;
+        mo[0] += 1.0;
+        mo[1] += fabs(m);
+        mo[2] += m2;
+        mo[3] += m2 * m2;
+        mo[4] += e;
+        mo[5] += e * e;
+    }
 }
 
 }  // namespace ising

@@ -92,6 +92,29 @@ struct NetState {
     float* wscale;         // [4] per-layer power-of-two weight scales of the e4m3 copy
 };
 
+// Swendsen-Wang step: per-lattice description (device, in the caller's SW
+// scratch).  Tiles are 64 x 32 sites (x in [64 tx, 64 tx + 64), y in
+// [32 ty, 32 ty + 32)), numbered row-major within a lattice and consecutively
+// over lattices.
+struct SwLat {
+    uint64_t word_off;     // first packed word of the lattice
+    uint64_t site_off;     // first label of the lattice (sum of the earlier L^2)
+    uint32_t L, wn, sim, key0, key1;
+    uint32_t thr;          // bond threshold floor(2^32 (1 - exp(-2/T))), clamped
+    uint32_t tile_begin;   // first tile of the lattice
+    uint32_t pad;
+};
+
+// Device pointers of one SW scratch area.
+struct SwState {
+    const SwLat* lat;
+    int n;
+    uint32_t total_tiles;
+    uint4* edges;          // [tiles] right-edge bonds (x), bottom-edge bonds (z | w << 32)
+    uint32_t* coins;       // [sites / 32] flip bit of every cluster root
+    uint32_t* label;       // [sites] parent pointers, finally the cluster root
+};
+
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_init_random(const DevState& st, int n_lat, cudaStream_t stream);
 cudaError_t launch_observables(const DevState& st, int n_lat, const uint32_t* lat_list,
@@ -134,6 +157,14 @@ cudaError_t launch_mh_apply(const DevState& st, const LearnedLat* ll, int n_lat,
                             uint32_t oy, const int8_t* win_old, const int8_t* win_new, const float* lq_old,
                             const float* lq_new, uint32_t round_t, unsigned long long* accepted,
                             cudaStream_t stream);
+
+// Swendsen-Wang launch wrappers (ising_cluster.cu).  sw_clusters: bonds,
+// labels and root coins of the current step; sw_flip: flip every cluster by
+// its root's coin; sw_record: E, M after the step into the trace / moments
+// and advance the device sweep counter.
+cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream);
+cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t stream);
+cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream);
 
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);

@@ -105,28 +105,7 @@ __device__ __forceinline__ void record(const DevState& st, uint32_t lat, uint32_
                                        unsigned long long sum_a, unsigned long long sum_pop,
                                        unsigned long long t) {
     const long long N = (long long)L * (long long)L;
-    const long long E = 2 * N - 2 * (long long)sum_a;
-    const long long M = N - 2 * (long long)sum_pop;
-    st.obs[2 * lat + 0] = E;
-    st.obs[2 * lat + 1] = M;
-    const long long cap = st.ctl->trace_cap;
-    if (cap > 0) {
-        const long long slot = (long long)(t % (unsigned long long)cap);
-        st.trace[((long long)lat * cap + slot) * 2 + 0] = E;
-        st.trace[((long long)lat * cap + slot) * 2 + 1] = M;
-    }
-    if (st.ctl->measure) {
-        const double inv = 1.0 / (double)N;
-        const double m = (double)M * inv, e = (double)E * inv;
-        const double m2 = m * m;
-        double* mo = st.mom + 6 * (size_t)lat;
-        mo[0] += 1.0;
-        mo[1] += fabs(m);
-        mo[2] += m2;
-        mo[3] += m2 * m2;
-        mo[4] += e;
-        mo[5] += e * e;
-    }
+    record_em(st, lat, L, 2 * N - 2 * (long long)sum_a, N - 2 * (long long)sum_pop, t);
 }
 
 // Block-wide sum of two counters; result valid in thread 0.

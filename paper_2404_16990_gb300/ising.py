@@ -115,6 +115,10 @@ def _load():
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), i64p], ctypes.c_int),
+            "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+            "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
+            "ising_sw_labels": ([vp, ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -446,6 +450,29 @@ def ising_learned_round(h, net: "IsingNet", round_index: int, sync: bool = True)
     return acc[:n]
 
 
+def ising_sw_scratch_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(_load().ising_sw_scratch_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def ising_sw_get_thresholds(h) -> np.ndarray:
+    thr = np.zeros(max(1, ising_num_sims(h)), dtype=np.uint32)
+    _check(_load().ising_sw_get_thresholds(h, _ptr(thr, ctypes.c_uint32)))
+    return thr[:ising_num_sims(h)]
+
+
+def ising_sw_sweep(h, n: int, dev_scratch: int, nbytes: int) -> None:
+    _check(_load().ising_sw_sweep(h, n, dev_scratch, nbytes))
+
+
+def ising_sw_labels(h, sim: int, dev_scratch: int, nbytes: int) -> np.ndarray:
+    L = ising_lattice_size(h, sim)
+    lab = np.zeros((max(L, 1), max(L, 1)), dtype=np.uint32)
+    _check(_load().ising_sw_labels(h, sim, dev_scratch, nbytes, _ptr(lab, ctypes.c_uint32)))
+    return lab
+
+
 class IsingSim:
     """Owner of one handle and its torch-allocated device workspace.
 
@@ -506,6 +533,25 @@ class IsingSim:
 
     def learned_round(self, net: "IsingNet", round_index: int, sync: bool = True):
         return ising_learned_round(self.h, net, round_index, sync)
+
+    def _sw_scratch(self):
+        if getattr(self, "sw_scratch", None) is None:
+            nbytes = ising_sw_scratch_bytes(self.h)
+            self.sw_scratch = self._torch.empty(max(nbytes, 256), dtype=self._torch.uint8,
+                                                device=self.workspace.device)
+        return self.sw_scratch.data_ptr(), self.sw_scratch.numel()
+
+    def sw_sweep(self, n: int) -> None:
+        """n Swendsen-Wang steps (scratch allocated once, on first use)."""
+        ptr, nbytes = self._sw_scratch()
+        ising_sw_sweep(self.h, n, ptr, nbytes)
+
+    def sw_labels(self, sim: int = 0) -> np.ndarray:
+        ptr, nbytes = self._sw_scratch()
+        return ising_sw_labels(self.h, sim, ptr, nbytes)
+
+    def sw_thresholds(self) -> np.ndarray:
+        return ising_sw_get_thresholds(self.h)
 
     def autotune(self, probe_sweeps: int = 10, force: bool = False) -> float:
         return ising_autotune(self.h, probe_sweeps, force)

@@ -111,3 +111,8 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ising_sweeps_done(None) == -1
     assert lib.ising_num_sims(None) == 0
     lib.ising_destroy(None)
+    sz = ctypes.c_size_t()
+    assert lib.ising_sw_scratch_bytes(None, ctypes.byref(sz)) == ising.ISING_EINVAL
+    assert lib.ising_sw_sweep(None, 1, None, 0) == ising.ISING_EINVAL
+    assert lib.ising_sw_labels(None, 0, None, 0, None) == ising.ISING_EINVAL
+    assert lib.ising_sw_get_thresholds(None, None) == ising.ISING_EINVAL
