@@ -944,7 +944,7 @@ void ising_destroy(ising_t h) {
 namespace {
 
 constexpr int kSwTileSites = 64 * 32;
-constexpr int kSwKernels = 7;   // local, merge, flatten, flip, observables (2), record
+constexpr int kSwKernels = 7;   // local, merge, resolve, flip, observables (2), record
 
 struct SwLayout {
     size_t lat = 0, edges = 0, coins = 0, label = 0, total = 0;
@@ -1095,7 +1095,8 @@ int ising_sw_labels(ising_t h, int sim, void* dev_scratch, size_t scratch_bytes,
     int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
     if (rc != ISING_OK) return rc;
     CUDA_TRY(launch_sw_clusters(h->st, sw, h->stream), "cluster labelling");
-    h->launches += 3;
+    CUDA_TRY(launch_sw_compress(sw, h->stream), "label compression");
+    h->launches += 4;
     const SwLat& d = h->sw_table[sim];
     CUDA_TRY(cudaMemcpyAsync(host_labels, sw.label + d.site_off, (size_t)d.L * d.L * sizeof(uint32_t),
                              cudaMemcpyDeviceToHost, h->stream), "copy labels");

@@ -20,11 +20,16 @@
 // to a smaller index (atomicMin on the larger root), so that a component's
 // final root is its smallest index:
 //   sw_local_kernel   one CTA per 64 x 32 tile: spins from the packed words,
-//                     bonds, union-find over the tile's internal bonds in
-//                     shared memory, global labels, the tile's edge bonds;
+//                     bonds; each row's runs of right bonds label themselves
+//                     by their first site, then one union per contact
+//                     between a run and the run below (shared memory); the
+//                     global labels (every site -> its tile-local root), a
+//                     bit mask of the tile-local roots and the edge bonds;
 //   sw_merge_kernel   unions over the bonds that cross tile edges (global);
-//   sw_flatten_kernel every site points at its root; coins of the roots;
-//   sw_flip_kernel    both colour words of (y, k) flipped by their roots' coins.
+//   sw_resolve_kernel every tile-local root -> its final root, whose coin it
+//                     takes over (one bit per tile-local root);
+//   sw_flip_kernel    both colour words of (y, k) flipped by the coin bit of
+//                     each site's tile-local root.
 // Every pointer walk and union retry is bounded; running past a bound (which
 // the strictly decreasing links make impossible for a consistent array) sets
 // the error word and leaves the labels in range.
@@ -38,7 +43,7 @@ namespace ising {
 namespace {
 
 constexpr int kTileW = 64, kTileH = 32, kTileSites = kTileW * kTileH;
-constexpr int kWordsPerTile = kTileSites / 32;     // flatten: one thread per 32 sites
+constexpr int kWordsPerTile = kTileSites / 32;     // resolve: one thread per 32 sites
 constexpr int kPairsPerTile = kTileSites / 64;     // flip: one thread per 64 sites
 constexpr int kEdgeSites = kTileH + kTileW;        // merge: right edge rows + bottom edge columns
 constexpr uint32_t kPhaseBond = 7u, kPhaseCoin = 8u;
@@ -80,11 +85,16 @@ __device__ __forceinline__ uint64_t natural_row(const uint32_t* base, uint32_t L
 }
 
 // --- union-find in shared memory (one tile, indices < kTileSites) ---------
-__device__ __forceinline__ uint32_t find_tile(const volatile uint32_t* lab, uint32_t x) {
-    uint32_t p = lab[x];
+// Path halving by atomicMin: a link only ever moves down to an ancestor, so a
+// walk ends within kTileSites steps.
+__device__ __forceinline__ uint32_t find_tile(uint32_t* lab, uint32_t x) {
+    const volatile uint32_t* v = lab;
+    uint32_t p = v[x];
     for (int it = 0; it < kTileSites && p != x; ++it) {
+        const uint32_t gp = v[p];
+        if (gp != p) atomicMin(&lab[x], gp);
         x = p;
-        p = lab[x];
+        p = gp;
     }
     return x;
 }
@@ -102,6 +112,7 @@ __device__ __forceinline__ void unite_tile(uint32_t* lab, uint32_t a, uint32_t b
 }
 
 // --- union-find in global memory (one lattice) ----------------------------
+// Path halving by atomicMin: a link only ever moves down to an ancestor.
 // Returns the root, or ~0u if the walk ran past its bound.
 __device__ __forceinline__ uint32_t find_global(uint32_t* lab, uint32_t x) {
     const volatile uint32_t* v = lab;
@@ -109,7 +120,7 @@ __device__ __forceinline__ uint32_t find_global(uint32_t* lab, uint32_t x) {
     for (int it = 0; it < kMaxChain; ++it) {
         if (p == x) return x;
         const uint32_t gp = v[p];
-        if (gp != p) atomicMin(&lab[x], gp);   // path halving; links only ever decrease
+        if (gp != p) atomicMin(&lab[x], gp);
         x = p;
         p = gp;
     }
@@ -132,23 +143,19 @@ __device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t
 
 // ---------------------------------------------------------------------------
 // Bonds and tile-local labels.  256 threads: thread (ly, seg) handles the 8
-// sites x0 + 8 seg .. + 7 of row y0 + ly (4 Philox blocks).
+// sites x0 + 8 seg .. + 7 of row y0 + ly (4 Philox blocks); the 8 threads of a
+// row are consecutive lanes of one warp.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) sw_local_kernel(DevState st, SwState sw) {
     __shared__ uint64_t s_row[kTileH + 1];
     __shared__ uint32_t s_rbit[kTileH + 1];
+    __shared__ uint64_t s_right[kTileH];    // bit i: bond (x0+i, y) - (x0+i+1, y); bit 63 leaves the tile
+    __shared__ uint64_t s_down[kTileH];     // bit i: bond (x0+i, y) - (x0+i, y+1); row 31 leaves the tile
     __shared__ uint32_t s_lab[kTileSites];
-    __shared__ uint32_t s_edge_r;
-    __shared__ unsigned long long s_edge_d;
     __shared__ int s_lat;
 
     const uint32_t tile = blockIdx.x;
-    if (threadIdx.x == 0) {
-        s_lat = lattice_of_tile(sw.lat, sw.n, tile);
-        s_edge_r = 0u;
-        s_edge_d = 0ull;
-    }
-    for (int i = threadIdx.x; i < kTileSites; i += blockDim.x) s_lab[i] = (uint32_t)i;
+    if (threadIdx.x == 0) s_lat = lattice_of_tile(sw.lat, sw.n, tile);
     __syncthreads();
     const SwLat d = sw.lat[s_lat];
     const uint32_t L = d.L, wn = d.wn;
@@ -184,28 +191,79 @@ __global__ void __launch_bounds__(256) sw_local_kernel(DevState st, SwState sw) 
     }
     b_r &= al_r;
     b_d &= al_d;
-
+    // whole-row bond masks from the row's 8 lanes
+    uint64_t R = (uint64_t)b_r << lx0, D = (uint64_t)b_d << lx0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        R |= __shfl_xor_sync(0xffffffffu, R, o);
+        D |= __shfl_xor_sync(0xffffffffu, D, o);
+    }
+    if (seg == 0) {
+        s_right[ly] = R;
+        s_down[ly] = D;
+    }
+    // runs of right bonds inside the row: every site points at the run's first
+    // site (bit j of `starts`: no bond from site j-1 into site j)
+    const uint64_t inner = R & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t starts = ~(inner << 1);
     const uint32_t i0 = ly * kTileW + lx0;
 #pragma unroll
     for (uint32_t j = 0; j < 8; ++j) {
-        if (((b_r >> j) & 1u) && lx0 + j < kTileW - 1) unite_tile(s_lab, i0 + j, i0 + j + 1);
-        if (((b_d >> j) & 1u) && ly < kTileH - 1) unite_tile(s_lab, i0 + j, i0 + j + kTileW);
+        const uint32_t x = lx0 + j;
+        const uint32_t first = 63u - (uint32_t)__clzll((long long)(starts & (~0ull >> (63u - x))));
+        s_lab[i0 + j] = ly * kTileW + first;
     }
-    if (seg == 7u && ((b_r >> 7) & 1u)) atomicOr(&s_edge_r, 1u << ly);
-    if (ly == kTileH - 1 && b_d) atomicOr(&s_edge_d, (unsigned long long)b_d << lx0);
     __syncthreads();
 
-    uint32_t out[8];
+    // one union per contact between a run and the run below: a down bond at x
+    // is skipped when the down bond at x - 1 joins the same two runs
+    if (ly < kTileH - 1) {
+        const uint64_t inner_below = s_right[ly + 1] & 0x7FFFFFFFFFFFFFFFull;
+        const uint64_t need = D & ~((D & inner & inner_below) << 1);
+        const uint32_t mine = (uint32_t)(need >> lx0) & 0xFFu;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j)
+            if ((mine >> j) & 1u) unite_tile(s_lab, i0 + j, i0 + j + kTileW);
+    }
+    __syncthreads();
+
+    // flatten by pointer jumping: every round points each site at its
+    // grandparent, so a chain of depth d is flat after ceil(log2 d) rounds
+    // (d < kTileSites = 2^11); no unions run any more
+#pragma unroll 1
+    for (int round = 0; round < 12; ++round) {
+        int changed = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t p = s_lab[i0 + j], gp = s_lab[p];
+            if (gp != p) {
+                s_lab[i0 + j] = gp;
+                changed = 1;
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    uint32_t out[8], roots = 0;
 #pragma unroll
     for (uint32_t j = 0; j < 8; ++j) {
-        const uint32_t r = find_tile(s_lab, i0 + j);
+        const uint32_t r = s_lab[i0 + j];
         out[j] = (y0 + (r >> 6)) * L + x0 + (r & 63u);
+        roots |= (uint32_t)(r == i0 + j) << j;
     }
     uint4* dst = reinterpret_cast<uint4*>(sw.label + d.site_off + p0);
     dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
     dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
-    if (threadIdx.x == 0)
-        sw.edges[tile] = make_uint4(s_edge_r, 0u, (uint32_t)s_edge_d, (uint32_t)(s_edge_d >> 32));
+    // tile-local roots as a bit mask in the coin array (32 sites = 4 lanes)
+    uint32_t mask = roots << (lx0 & 31u);
+    mask |= __shfl_xor_sync(0xffffffffu, mask, 1);
+    mask |= __shfl_xor_sync(0xffffffffu, mask, 2);
+    if ((seg & 3u) == 0) sw.coins[(d.site_off + p0) / 32] = mask;
+    if (threadIdx.x == 0) {
+        uint32_t edge_r = 0;
+        for (int r = 0; r < kTileH; ++r) edge_r |= (uint32_t)(s_right[r] >> 63) << r;
+        const uint64_t edge_d = s_down[kTileH - 1];
+        sw.edges[tile] = make_uint4(edge_r, 0u, (uint32_t)edge_d, (uint32_t)(edge_d >> 32));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -239,38 +297,52 @@ __global__ void __launch_bounds__(256) sw_merge_kernel(DevState st, SwState sw) 
 }
 
 // ---------------------------------------------------------------------------
-// Every site points at its root; roots draw their coins.  One thread per 32
+// Every tile-local root (bit mask left in the coin array by sw_local_kernel)
+// is resolved to its final root f and takes f's coin (the top bit of lane
+// f & 3 of block f >> 2), which replaces the mask bit; the flip then needs
+// only the coin bit of each site's tile-local root.  One thread per 32
 // consecutive sites (one coin word).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) sw_flatten_kernel(DevState st, SwState sw) {
+__global__ void __launch_bounds__(256) sw_resolve_kernel(DevState st, SwState sw) {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (uint64_t)sw.total_tiles * kWordsPerTile) return;
     const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)(g / kWordsPerTile))];
     const uint32_t w = (uint32_t)(g - (uint64_t)d.tile_begin * kWordsPerTile);   // word within the lattice
     uint32_t* lab = sw.label + d.site_off;
+    uint32_t* coin_word = sw.coins + d.site_off / 32 + w;
     const uint32_t t = (uint32_t)st.ctl->t;
-    uint32_t coin = 0;
+    uint32_t m = *coin_word, coin = 0;
     bool failed = false;
-#pragma unroll 2
-    for (uint32_t j = 0; j < 32; j += 4) {
-        uint32_t roots = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < 4; ++i) {
-            const uint32_t p = 32u * w + j + i;
-            const uint32_t r = find_global(lab, p);
-            if (r == ~0u) { failed = true; continue; }
-            lab[p] = r;
-            if (r == p) roots |= 1u << i;
+    while (m) {
+        const uint32_t i = (uint32_t)__ffs(m) - 1u;
+        m &= m - 1u;
+        const uint32_t r = 32u * w + i;
+        const uint32_t f = find_global(lab, r);
+        if (f == ~0u) {
+            failed = true;
+            continue;
         }
-        if (roots) {
-            const uint4 v = philox((32u * w + j) >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
-            const uint32_t c = ((v.x >> 31) & roots) | (((v.y >> 31) << 1) & roots) |
-                               (((v.z >> 31) << 2) & roots) | (((v.w >> 31) << 3) & roots);
-            coin |= c << j;
-        }
+        if (f != r) lab[r] = f;
+        const uint4 v = philox(f >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
+        const uint32_t lane = f & 3u;
+        const uint32_t word = lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+        coin |= (word >> 31) << i;
     }
     if (failed) atomicExch(&st.ctl->error, kErrUnionBound);
-    sw.coins[d.site_off / 32 + w] = coin;
+    *coin_word = coin;
+}
+
+// Every site points at its final root (only for ising_sw_labels): the link
+// of a site is a tile-local root (of its own tile, or of another one after a
+// path-halving step of the merge), whose link is final after
+// sw_resolve_kernel.
+__global__ void __launch_bounds__(256) sw_compress_kernel(SwState sw, uint64_t sites) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= sites) return;
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)(g / kTileSites))];
+    uint32_t* lab = sw.label + d.site_off;
+    const uint32_t p = (uint32_t)(g - d.site_off);
+    lab[p] = lab[lab[p]];
 }
 
 // ---------------------------------------------------------------------------
@@ -285,7 +357,7 @@ __global__ void __launch_bounds__(256) sw_flip_kernel(DevState st, SwState sw) {
     const uint32_t y = i / wn, k = i - y * wn;
     const uint32_t p0 = y * L + 64u * k;
     const uint4* lab = reinterpret_cast<const uint4*>(sw.label + d.site_off + p0);
-    const uint32_t* coins = sw.coins + d.site_off / 32;
+    const uint32_t* coins = sw.coins + d.site_off / 32;   // coin of each tile-local root's cluster
     uint32_t m_even = 0, m_odd = 0;
 #pragma unroll 4
     for (uint32_t q = 0; q < 16; ++q) {
@@ -325,7 +397,14 @@ cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t words = (uint64_t)sw.total_tiles * kWordsPerTile;
-    sw_flatten_kernel<<<(unsigned)((words + 255) / 256), 256, 0, stream>>>(st, sw);
+    sw_resolve_kernel<<<(unsigned)((words + 255) / 256), 256, 0, stream>>>(st, sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_compress(const SwState& sw, cudaStream_t stream) {
+    if (sw.n <= 0 || sw.total_tiles == 0) return cudaSuccess;
+    const uint64_t sites = (uint64_t)sw.total_tiles * kTileSites;
+    sw_compress_kernel<<<(unsigned)((sites + 255) / 256), 256, 0, stream>>>(sw, sites);
     return cudaGetLastError();
 }
 

@@ -111,8 +111,8 @@ struct SwState {
     int n;
     uint32_t total_tiles;
     uint4* edges;          // [tiles] right-edge bonds (x), bottom-edge bonds (z | w << 32)
-    uint32_t* coins;       // [sites / 32] flip bit of every cluster root
-    uint32_t* label;       // [sites] parent pointers, finally the cluster root
+    uint32_t* coins;       // [sites / 32] tile-local root mask, then each tile-local root's cluster coin
+    uint32_t* label;       // [sites] parent pointers (site -> tile-local root -> cluster root)
 };
 
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
@@ -159,12 +159,13 @@ cudaError_t launch_mh_apply(const DevState& st, const LearnedLat* ll, int n_lat,
                             cudaStream_t stream);
 
 // Swendsen-Wang launch wrappers (ising_cluster.cu).  sw_clusters: bonds,
-// labels and root coins of the current step; sw_flip: flip every cluster by
-// its root's coin; sw_record: E, M after the step into the trace / moments
+// labels (every site -> a tile-local root -> the final root) and the root
+// coins of the current step; sw_flip: flip every cluster by its root's coin; sw_record: E, M after the step into the trace / moments
 // and advance the device sweep counter.
 cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream);
 cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t stream);
 cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream);
+cudaError_t launch_sw_compress(const SwState& sw, cudaStream_t stream);   // labels -> final roots
 
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);
