@@ -386,7 +386,7 @@ int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls, const dou
 #define ISING_SW_MAX_L 32768
 
 /* Bytes of device scratch one cluster step of this handle needs: the
- * per-lattice table, 16 bytes per 64 x 32 tile, one coin bit and one 32-bit
+ * per-lattice table, 16 bytes per 64 x 16 tile, one coin bit and one 32-bit
  * label per site (about 4.14 bytes per site).  ISING_EINVAL if a lattice has
  * L > ISING_SW_MAX_L. */
 int ising_sw_scratch_bytes(ising_t h, size_t* bytes);

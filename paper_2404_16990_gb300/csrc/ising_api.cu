@@ -943,7 +943,7 @@ void ising_destroy(ising_t h) {
 // ===========================================================================
 namespace {
 
-constexpr int kSwTileSites = 64 * 32;
+constexpr int kSwTileSites = kSwTileW * kSwTileH;
 constexpr int kSwKernels = 7;   // local, merge, resolve, flip, observables (2), record
 
 struct SwLayout {

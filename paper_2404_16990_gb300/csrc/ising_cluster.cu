@@ -19,7 +19,7 @@
 // Labelling is a lock-free union-find whose links always point from a larger
 // to a smaller index (atomicMin on the larger root), so that a component's
 // final root is its smallest index:
-//   sw_local_kernel   one CTA per 64 x 32 tile: spins from the packed words,
+//   sw_local_kernel   one CTA per 64 x kSwTileH tile: spins from the packed words,
 //                     bonds; each row's runs of right bonds label themselves
 //                     by their first site, then one union per contact
 //                     between a run and the run below (shared memory); the
@@ -42,7 +42,8 @@
 namespace ising {
 namespace {
 
-constexpr int kTileW = 64, kTileH = 32, kTileSites = kTileW * kTileH;
+constexpr int kTileW = kSwTileW, kTileH = kSwTileH, kTileSites = kTileW * kTileH;
+static_assert(kTileW == 64 && kTileH <= 32 && kSwThreads % 32 == 0, "one 64-bit word per tile row, edge rows in 32 bits");
 constexpr int kWordsPerTile = kTileSites / 32;     // resolve: one thread per 32 sites
 constexpr int kPairsPerTile = kTileSites / 64;     // flip: one thread per 64 sites
 constexpr int kEdgeSites = kTileH + kTileW;        // merge: right edge rows + bottom edge columns
@@ -142,11 +143,11 @@ __device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Bonds and tile-local labels.  256 threads: thread (ly, seg) handles the 8
+// Bonds and tile-local labels.  8 threads per row: thread (ly, seg) handles the 8
 // sites x0 + 8 seg .. + 7 of row y0 + ly (4 Philox blocks); the 8 threads of a
 // row are consecutive lanes of one warp.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) sw_local_kernel(DevState st, SwState sw) {
+__global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwState sw) {
     __shared__ uint64_t s_row[kTileH + 1];
     __shared__ uint32_t s_rbit[kTileH + 1];
     __shared__ uint64_t s_right[kTileH];    // bit i: bond (x0+i, y) - (x0+i+1, y); bit 63 leaves the tile
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) sw_local_kernel(DevState st, SwState sw) 
     const uint32_t* base = st.spins + d.word_off;
     const uint32_t t = (uint32_t)st.ctl->t;
 
-    // rows y0 .. y0 + 32 (the last wraps at the lattice edge) and, for each,
+    // rows y0 .. y0 + kTileH (the last wraps at the lattice edge) and, for each,
     // the site just right of the tile (x = 64 (tx + 1) mod L: even, colour y & 1)
     if (threadIdx.x <= kTileH) {
         uint32_t y = y0 + threadIdx.x;
@@ -389,7 +390,7 @@ __global__ void sw_record_kernel(DevState st, int n_lat) {
 
 cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream) {
     if (sw.n <= 0 || sw.total_tiles == 0) return cudaSuccess;
-    sw_local_kernel<<<sw.total_tiles, 256, 0, stream>>>(st, sw);
+    sw_local_kernel<<<sw.total_tiles, kSwThreads, 0, stream>>>(st, sw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t edge_threads = (uint64_t)sw.total_tiles * kEdgeSites;

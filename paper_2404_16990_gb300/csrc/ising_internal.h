@@ -92,10 +92,15 @@ struct NetState {
     float* wscale;         // [4] per-layer power-of-two weight scales of the e4m3 copy
 };
 
-// Swendsen-Wang step: per-lattice description (device, in the caller's SW
-// scratch).  Tiles are 64 x 32 sites (x in [64 tx, 64 tx + 64), y in
-// [32 ty, 32 ty + 32)), numbered row-major within a lattice and consecutively
-// over lattices.
+// Swendsen-Wang step: tiles of kSwTileW x kSwTileH sites (x in [64 tx,
+// 64 tx + 64), y in [kSwTileH ty, kSwTileH (ty + 1))), numbered row-major
+// within a lattice and consecutively over lattices; one CTA of 8 threads per
+// tile row labels a tile.
+constexpr int kSwTileW = 64;
+constexpr int kSwTileH = 16;
+constexpr int kSwThreads = 8 * kSwTileH;
+
+// Per-lattice description (device, in the caller's SW scratch).
 struct SwLat {
     uint64_t word_off;     // first packed word of the lattice
     uint64_t site_off;     // first label of the lattice (sum of the earlier L^2)

@@ -3,8 +3,9 @@ sampler snapshots, then integrated autocorrelation times and effective
 independent samples per second of |M| and E at equal observables.
 
 Workload (per temperature): `replicas` lattices of side L (defaults 64 x
-256^2) from random starts; `burn` plain sweeps; `n_snap` snapshots (one every
-`snap_every` sweeps, all replicas at once) form the training pool; the net is
+256^2) from random starts, equilibrated by `sw_burn` Swendsen-Wang steps and
+`burn` plain sweeps; `n_snap` snapshots (one every `snap_every` sweeps, all
+replicas at once) form the training pool; the net is
 trained with Adam on random 10x10 windows of the pool; then two chains start
 from the same equilibrated state:
   plain    one unit = one checkerboard sweep
@@ -67,7 +68,7 @@ def _obs_stats(E, M, N):
 
 def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000, n_snap: int = 20000,
                     snap_every: int = 10, train_steps: int = 1500, batch: int = 512, lr: float = 3e-3,
-                    units: int = 20000, seed: int = 2024, verbose: bool = True) -> dict:
+                    units: int = 20000, sw_burn: int = 500, seed: int = 2024, verbose: bool = True) -> dict:
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)
@@ -75,6 +76,7 @@ def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000
     res = {"T": T, "L": L, "replicas": replicas}
     with torch.cuda.stream(stream):
         sim = ising.IsingSim(L, [T] * replicas, seed, trace_cap=units, stream=stream)
+        sim.sw_sweep(sw_burn)                           # cluster steps equilibrate fast at and below T_c
         sim.sweep(burn)
         per = L * L // 8
         sets = max(1, n_snap // replicas)
