@@ -19,12 +19,13 @@
 // Labelling is a lock-free union-find whose links always point from a larger
 // to a smaller index (atomicMin on the larger root), so that a component's
 // final root is its smallest index:
-//   sw_local_kernel   one CTA per 64 x kSwTileH tile: spins from the packed words,
-//                     bonds; each row's runs of right bonds label themselves
-//                     by their first site, then one union per contact
-//                     between a run and the run below (shared memory); the
-//                     global labels (every site -> its tile-local root), a
-//                     bit mask of the tile-local roots and the edge bonds;
+//   sw_local_kernel   one warp per 64 x kSwTileH tile, rows in order: spins
+//                     from the packed words, bonds; each row's runs of right
+//                     bonds label themselves by their first site and join
+//                     the runs above through the down bonds (union-find in
+//                     shared memory); the global labels (every site -> its
+//                     tile-local root), a bit mask of the tile-local roots
+//                     and the edge bonds;
 //   sw_merge_kernel   unions over the bonds that cross tile edges (global);
 //   sw_resolve_kernel every tile-local root -> its final root, whose coin it
 //                     takes over (one bit per tile-local root);
@@ -62,6 +63,9 @@ __device__ __forceinline__ int lattice_of_tile(const SwLat* lat, int n, uint32_t
     }
     return lo;
 }
+
+// Bit l of the result = pred of lane l (whole warp).
+__device__ __forceinline__ uint32_t ballot_bit(bool pred) { return __ballot_sync(0xffffffffu, pred); }
 
 // The 32 bits of v moved to the even bit positions of a 64-bit word.
 __device__ __forceinline__ uint64_t spread_even(uint32_t v) {
@@ -143,126 +147,126 @@ __device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Bonds and tile-local labels.  8 threads per row: thread (ly, seg) handles the 8
-// sites x0 + 8 seg .. + 7 of row y0 + ly (4 Philox blocks); the 8 threads of a
-// row are consecutive lanes of one warp.
+// Bonds and tile-local labels: one warp per tile, rows in order.  Lane l owns
+// the sites x0 + 2l and x0 + 2l + 1 of every row, whose four bond draws are
+// one Philox block (q = p >> 1 with p = y*L + x0 + 2l even).  Row k: the
+// row's right / down bond masks come from two ballots each; every site of a
+// run of right bonds is labelled by the run's first site; the runs are joined
+// to the runs of row k - 1 through the down bonds of row k - 1 (one union per
+// pair of runs, lanes in parallel); row k is then flattened.  Unions of a
+// later row can join earlier roots, so the tile is flattened once more at the
+// end by pointer jumping.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwState sw) {
-    __shared__ uint64_t s_row[kTileH + 1];
-    __shared__ uint32_t s_rbit[kTileH + 1];
-    __shared__ uint64_t s_right[kTileH];    // bit i: bond (x0+i, y) - (x0+i+1, y); bit 63 leaves the tile
-    __shared__ uint64_t s_down[kTileH];     // bit i: bond (x0+i, y) - (x0+i, y+1); row 31 leaves the tile
-    __shared__ uint32_t s_lab[kTileSites];
-    __shared__ int s_lat;
+constexpr int kTilesPerBlock = kSwThreads / 32;
 
-    const uint32_t tile = blockIdx.x;
-    if (threadIdx.x == 0) s_lat = lattice_of_tile(sw.lat, sw.n, tile);
-    __syncthreads();
-    const SwLat d = sw.lat[s_lat];
+__global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwState sw) {
+    __shared__ uint32_t s_lab[kTilesPerBlock][kTileSites];
+    __shared__ uint64_t s_row[kTilesPerBlock][kTileH + 1];   // natural-order spins of rows y0 .. y0 + kTileH
+    __shared__ uint64_t s_R[kTilesPerBlock][kTileH];         // right bonds per row (bit 63 leaves the tile)
+    __shared__ uint64_t s_D[kTilesPerBlock][kTileH];         // down bonds per row (the last row leaves it)
+    __shared__ uint32_t s_rbit[kTilesPerBlock][kTileH];      // spin of the site right of the tile, per row
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t tile = blockIdx.x * kTilesPerBlock + warp;
+    if (tile >= sw.total_tiles) return;              // whole warps only; no block barrier below
+    uint32_t* lab = s_lab[warp];
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, tile)];
     const uint32_t L = d.L, wn = d.wn;
     const uint32_t local = tile - d.tile_begin;
     const uint32_t tx = local % wn, ty = local / wn;     // L / 64 tiles per tile row
     const uint32_t x0 = kTileW * tx, y0 = kTileH * ty;
     const uint32_t* base = st.spins + d.word_off;
     const uint32_t t = (uint32_t)st.ctl->t;
+    const uint32_t xe = 2u * lane, xo = xe + 1u;
 
-    // rows y0 .. y0 + kTileH (the last wraps at the lattice edge) and, for each,
-    // the site just right of the tile (x = 64 (tx + 1) mod L: even, colour y & 1)
-    if (threadIdx.x <= kTileH) {
-        uint32_t y = y0 + threadIdx.x;
+    // all rows of the tile at once (the last one wraps at the lattice edge)
+    if (lane <= (uint32_t)kTileH) {
+        uint32_t y = y0 + lane;
         if (y >= L) y -= L;
-        s_row[threadIdx.x] = natural_row(base, L, wn, y, tx);
-        const uint32_t kr = (tx + 1 == wn) ? 0u : tx + 1;
-        s_rbit[threadIdx.x] = base[((size_t)(y & 1u) * L + y) * wn + kr] & 1u;
+        s_row[warp][lane] = natural_row(base, L, wn, y, tx);
+        if (lane < (uint32_t)kTileH) {
+            const uint32_t kr = (tx + 1 == wn) ? 0u : tx + 1;   // x = 64 kr: even, colour y & 1
+            s_rbit[warp][lane] = base[((size_t)(y & 1u) * L + y) * wn + kr] & 1u;
+        }
     }
-    __syncthreads();
+    __syncwarp();
+    // bonds of every row: the four draws of lane l's two sites are one block
+#pragma unroll 4
+    for (uint32_t k = 0; k < (uint32_t)kTileH; ++k) {
+        const uint64_t row = s_row[warp][k], below = s_row[warp][k + 1];
+        const uint64_t al_r = ~(row ^ ((row >> 1) | ((uint64_t)s_rbit[warp][k] << 63)));
+        const uint64_t al_d = ~(row ^ below);
+        const uint32_t p = (y0 + k) * L + x0 + xe;
+        const uint4 r = philox(p >> 1, t, d.sim, kPhaseBond, d.key0, d.key1);
+        const uint32_t re = ballot_bit(((al_r >> xe) & 1u) && r.x < d.thr);
+        const uint32_t ro = ballot_bit(((al_r >> xo) & 1u) && r.z < d.thr);
+        const uint32_t de = ballot_bit(((al_d >> xe) & 1u) && r.y < d.thr);
+        const uint32_t dd = ballot_bit(((al_d >> xo) & 1u) && r.w < d.thr);
+        if (lane == 0) {
+            s_R[warp][k] = spread_even(re) | (spread_even(ro) << 1);
+            s_D[warp][k] = spread_even(de) | (spread_even(dd) << 1);
+        }
+    }
+    __syncwarp();
 
-    const uint32_t ly = threadIdx.x >> 3, seg = threadIdx.x & 7u, lx0 = 8u * seg;
-    const uint64_t row = s_row[ly], below = s_row[ly + 1];
-    const uint64_t right = (row >> 1) | ((uint64_t)s_rbit[ly] << 63);
-    const uint32_t al_r = (uint32_t)(~(row ^ right) >> lx0) & 0xFFu;   // equal to the right neighbour
-    const uint32_t al_d = (uint32_t)(~(row ^ below) >> lx0) & 0xFFu;   // equal to the neighbour below
-    const uint32_t p0 = (y0 + ly) * L + x0 + lx0;                      // even
-    uint32_t b_r = 0, b_d = 0;
-#pragma unroll
-    for (uint32_t j = 0; j < 4; ++j) {
-        const uint4 r = philox((p0 >> 1) + j, t, d.sim, kPhaseBond, d.key0, d.key1);
-        b_r |= ((uint32_t)(r.x < d.thr) << (2 * j)) | ((uint32_t)(r.z < d.thr) << (2 * j + 1));
-        b_d |= ((uint32_t)(r.y < d.thr) << (2 * j)) | ((uint32_t)(r.w < d.thr) << (2 * j + 1));
+    // rows in order: runs label themselves, join the runs above, flatten
+    const uint64_t upto_e = ~0ull >> (63u - xe), upto_o = ~0ull >> (63u - xo);
+    uint64_t inner_prev = 0;
+#pragma unroll 1
+    for (uint32_t k = 0; k < (uint32_t)kTileH; ++k) {
+        const uint64_t inner = s_R[warp][k] & 0x7FFFFFFFFFFFFFFFull;
+        const uint64_t starts = ~(inner << 1);         // bit j: no bond into site j
+        const uint32_t i0 = k * kTileW;
+        lab[i0 + xe] = i0 + 63u - (uint32_t)__clzll((long long)(starts & upto_e));
+        lab[i0 + xo] = i0 + 63u - (uint32_t)__clzll((long long)(starts & upto_o));
+        __syncwarp();
+        if (k > 0) {
+            // one contact per pair of runs: a down bond at x is skipped when
+            // the down bond at x - 1 joins the same two runs
+            const uint64_t down = s_D[warp][k - 1];
+            const uint64_t need = down & ~((down & inner_prev & inner) << 1);
+            if ((need >> xe) & 1u) unite_tile(lab, i0 - kTileW + xe, i0 + xe);
+            if ((need >> xo) & 1u) unite_tile(lab, i0 - kTileW + xo, i0 + xo);
+            __syncwarp();
+            const uint32_t fe = find_tile(lab, i0 + xe), fo = find_tile(lab, i0 + xo);
+            __syncwarp();
+            lab[i0 + xe] = fe;
+            lab[i0 + xo] = fo;
+            __syncwarp();
+        }
+        inner_prev = inner;
     }
-    b_r &= al_r;
-    b_d &= al_d;
-    // whole-row bond masks from the row's 8 lanes
-    uint64_t R = (uint64_t)b_r << lx0, D = (uint64_t)b_d << lx0;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        R |= __shfl_xor_sync(0xffffffffu, R, o);
-        D |= __shfl_xor_sync(0xffffffffu, D, o);
-    }
-    if (seg == 0) {
-        s_right[ly] = R;
-        s_down[ly] = D;
-    }
-    // runs of right bonds inside the row: every site points at the run's first
-    // site (bit j of `starts`: no bond from site j-1 into site j)
-    const uint64_t inner = R & 0x7FFFFFFFFFFFFFFFull;
-    const uint64_t starts = ~(inner << 1);
-    const uint32_t i0 = ly * kTileW + lx0;
-#pragma unroll
-    for (uint32_t j = 0; j < 8; ++j) {
-        const uint32_t x = lx0 + j;
-        const uint32_t first = 63u - (uint32_t)__clzll((long long)(starts & (~0ull >> (63u - x))));
-        s_lab[i0 + j] = ly * kTileW + first;
-    }
-    __syncthreads();
-
-    // one union per contact between a run and the run below: a down bond at x
-    // is skipped when the down bond at x - 1 joins the same two runs
-    if (ly < kTileH - 1) {
-        const uint64_t inner_below = s_right[ly + 1] & 0x7FFFFFFFFFFFFFFFull;
-        const uint64_t need = D & ~((D & inner & inner_below) << 1);
-        const uint32_t mine = (uint32_t)(need >> lx0) & 0xFFu;
-#pragma unroll
-        for (uint32_t j = 0; j < 8; ++j)
-            if ((mine >> j) & 1u) unite_tile(s_lab, i0 + j, i0 + j + kTileW);
-    }
-    __syncthreads();
-
-    // flatten by pointer jumping: every round points each site at its
-    // grandparent, so a chain of depth d is flat after ceil(log2 d) rounds
-    // (d < kTileSites = 2^11); no unions run any more
+    // final flatten by pointer jumping (depth < kTileSites <= 2^11)
 #pragma unroll 1
     for (int round = 0; round < 12; ++round) {
-        int changed = 0;
-#pragma unroll
-        for (uint32_t j = 0; j < 8; ++j) {
-            const uint32_t p = s_lab[i0 + j], gp = s_lab[p];
-            if (gp != p) {
-                s_lab[i0 + j] = gp;
-                changed = 1;
+        bool changed = false;
+        for (uint32_t i = lane; i < (uint32_t)kTileSites; i += 32u) {
+            const uint32_t q = lab[i], gq = lab[q];
+            if (gq != q) {
+                lab[i] = gq;
+                changed = true;
             }
         }
-        if (!__syncthreads_or(changed)) break;
+        if (!__any_sync(0xffffffffu, changed)) break;
+        __syncwarp();
     }
-    uint32_t out[8], roots = 0;
-#pragma unroll
-    for (uint32_t j = 0; j < 8; ++j) {
-        const uint32_t r = s_lab[i0 + j];
-        out[j] = (y0 + (r >> 6)) * L + x0 + (r & 63u);
-        roots |= (uint32_t)(r == i0 + j) << j;
+    __syncwarp();
+    // global labels (site -> tile-local root), root mask, edge bonds
+    uint32_t* glab = sw.label + d.site_off;
+#pragma unroll 4
+    for (uint32_t k = 0; k < (uint32_t)kTileH; ++k) {
+        const uint32_t i0 = k * kTileW;
+        const uint32_t re = lab[i0 + xe], ro = lab[i0 + xo];
+        const uint32_t pe = (y0 + k) * L + x0 + xe;
+        *reinterpret_cast<uint2*>(glab + pe) = make_uint2((y0 + (re >> 6)) * L + x0 + (re & 63u),
+                                                          (y0 + (ro >> 6)) * L + x0 + (ro & 63u));
+        const uint64_t roots = spread_even(ballot_bit(re == i0 + xe)) |
+                               (spread_even(ballot_bit(ro == i0 + xo)) << 1);
+        if (lane < 2) sw.coins[(d.site_off + (uint64_t)(y0 + k) * L + x0) / 32 + lane] = (uint32_t)(roots >> (32 * lane));
     }
-    uint4* dst = reinterpret_cast<uint4*>(sw.label + d.site_off + p0);
-    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
-    // tile-local roots as a bit mask in the coin array (32 sites = 4 lanes)
-    uint32_t mask = roots << (lx0 & 31u);
-    mask |= __shfl_xor_sync(0xffffffffu, mask, 1);
-    mask |= __shfl_xor_sync(0xffffffffu, mask, 2);
-    if ((seg & 3u) == 0) sw.coins[(d.site_off + p0) / 32] = mask;
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         uint32_t edge_r = 0;
-        for (int r = 0; r < kTileH; ++r) edge_r |= (uint32_t)(s_right[r] >> 63) << r;
-        const uint64_t edge_d = s_down[kTileH - 1];
+        for (int k = 0; k < kTileH; ++k) edge_r |= (uint32_t)(s_R[warp][k] >> 63) << k;
+        const uint64_t edge_d = s_D[warp][kTileH - 1];
         sw.edges[tile] = make_uint4(edge_r, 0u, (uint32_t)edge_d, (uint32_t)(edge_d >> 32));
     }
 }
@@ -390,7 +394,7 @@ __global__ void sw_record_kernel(DevState st, int n_lat) {
 
 cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream) {
     if (sw.n <= 0 || sw.total_tiles == 0) return cudaSuccess;
-    sw_local_kernel<<<sw.total_tiles, kSwThreads, 0, stream>>>(st, sw);
+    sw_local_kernel<<<(sw.total_tiles + kTilesPerBlock - 1) / kTilesPerBlock, kSwThreads, 0, stream>>>(st, sw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t edge_threads = (uint64_t)sw.total_tiles * kEdgeSites;

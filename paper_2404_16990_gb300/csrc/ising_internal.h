@@ -94,11 +94,11 @@ struct NetState {
 
 // Swendsen-Wang step: tiles of kSwTileW x kSwTileH sites (x in [64 tx,
 // 64 tx + 64), y in [kSwTileH ty, kSwTileH (ty + 1))), numbered row-major
-// within a lattice and consecutively over lattices; one CTA of 8 threads per
-// tile row labels a tile.
+// within a lattice and consecutively over lattices; one warp labels a tile,
+// kSwThreads / 32 tiles per CTA.
 constexpr int kSwTileW = 64;
 constexpr int kSwTileH = 16;
-constexpr int kSwThreads = 8 * kSwTileH;
+constexpr int kSwThreads = 128;
 
 // Per-lattice description (device, in the caller's SW scratch).
 struct SwLat {
