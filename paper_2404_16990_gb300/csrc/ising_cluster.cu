@@ -153,9 +153,8 @@ __device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t
 // row's right / down bond masks come from two ballots each; every site of a
 // run of right bonds is labelled by the run's first site; the runs are joined
 // to the runs of row k - 1 through the down bonds of row k - 1 (one union per
-// pair of runs, lanes in parallel); row k is then flattened.  Unions of a
-// later row can join earlier roots, so the tile is flattened once more at the
-// end by pointer jumping.
+// pair of runs, lanes in parallel).  The tile is flattened at the end by
+// pointer jumping.
 // ---------------------------------------------------------------------------
 constexpr int kTilesPerBlock = kSwThreads / 32;
 
@@ -208,7 +207,7 @@ __global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwSta
     }
     __syncwarp();
 
-    // rows in order: runs label themselves, join the runs above, flatten
+    // rows in order: runs label themselves and join the runs above
     const uint64_t upto_e = ~0ull >> (63u - xe), upto_o = ~0ull >> (63u - xo);
     uint64_t inner_prev = 0;
 #pragma unroll 1
@@ -226,11 +225,6 @@ __global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwSta
             const uint64_t need = down & ~((down & inner_prev & inner) << 1);
             if ((need >> xe) & 1u) unite_tile(lab, i0 - kTileW + xe, i0 + xe);
             if ((need >> xo) & 1u) unite_tile(lab, i0 - kTileW + xo, i0 + xo);
-            __syncwarp();
-            const uint32_t fe = find_tile(lab, i0 + xe), fo = find_tile(lab, i0 + xo);
-            __syncwarp();
-            lab[i0 + xe] = fe;
-            lab[i0 + xo] = fo;
             __syncwarp();
         }
         inner_prev = inner;
