@@ -44,3 +44,41 @@ def moments(E, M, N):
     m = np.asarray(M, dtype=np.float64) / N
     e = np.asarray(E, dtype=np.float64) / N
     return np.array([len(m), np.abs(m).sum(), (m ** 2).sum(), (m ** 4).sum(), e.sum(), (e ** 2).sum()])
+
+
+def statistical_inefficiency(x):
+    """g = 1 + 2 tau with tau = sum_{t>=1} (1 - t/T) C(t), where C(t) is the
+    normalised fluctuation autocorrelation of the series about its own mean,
+    C(t) = [sum_{n<T-t} d_n d_{n+t} / (T - t)] / [sum_n d_n^2 / T], and the sum
+    stops before the first lag with C(t) <= 0; g is at least 1 (Chodera,
+    J. Chem. Theory Comput. 12, 1799 (2016), the method Section 3.1 uses to
+    discard non-equilibrated data).  One lag at a time."""
+    a = np.asarray(x, dtype=np.float64)
+    T = len(a)
+    d = a - a.mean()
+    var = float(np.dot(d, d)) / T
+    if not var > 0.0:
+        return 1.0
+    tau = 0.0
+    for t in range(1, T):
+        C = float(np.dot(d[:T - t], d[t:])) / ((T - t) * var)
+        if C <= 0.0:
+            break
+        tau += (1.0 - t / T) * C
+    return max(1.0, 1.0 + 2.0 * tau)
+
+
+def detect_equilibration(x, stride: int = 1):
+    """Automatic equilibration detection (same reference): for every candidate
+    start t0 = 0, stride, 2 stride, ... (at most T - 2), the effective number
+    of samples of x[t0:] is N(t0) = (T - t0) / g(x[t0:]); the result is the
+    t0 with the largest N (the smallest such t0 on ties), with its g and N."""
+    a = np.asarray(x, dtype=np.float64)
+    T = len(a)
+    best = (-1.0, 0, 1.0)
+    for t0 in range(0, T - 1, max(1, int(stride))):
+        g = statistical_inefficiency(a[t0:])
+        n_eff = (T - t0) / g
+        if n_eff > best[0]:
+            best = (n_eff, t0, g)
+    return best[1], best[2], best[0]

@@ -76,3 +76,59 @@ def test_library_binder_matches_oracle():
     for k in range(5):
         assert abs(U[k] - ostats.binder(ms[k])) < 1e-12
     assert math.isnan(U[5])
+
+
+# --------------------------------------------------------------------------
+# Statistical inefficiency and automatic equilibration detection (the method
+# Section 3.1 cites for discarding non-equilibrated data).
+# --------------------------------------------------------------------------
+def test_statistical_inefficiency_worked_case():
+    # x = 1, 2, 3, 4: mean 2.5, deviations -1.5, -0.5, 0.5, 1.5, variance 1.25;
+    # C(1) = (0.75 - 0.25 + 0.75) / (3 * 1.25) = 1/3, C(2) = (-0.75 - 0.75) /
+    # (2 * 1.25) < 0 stops the sum; g = 1 + 2 (1 - 1/4) (1/3) = 1.5
+    assert abs(ostats.statistical_inefficiency([1.0, 2.0, 3.0, 4.0]) - 1.5) < 1e-15
+    # anticorrelated: C(1) < 0 at once, g = 1; constant: g = 1
+    assert ostats.statistical_inefficiency([1.0, -1.0] * 50) == 1.0
+    assert ostats.statistical_inefficiency(np.full(10, 3.0)) == 1.0
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9])
+def test_statistical_inefficiency_ar1_closed_form(rho):
+    # g = 1 + 2 tau = (1 + rho) / (1 - rho) for AR(1)
+    x = ar1(rho, 200_000, seed=40 + int(rho * 10))
+    g = ostats.statistical_inefficiency(x)
+    exact = (1 + rho) / (1 - rho)
+    assert abs(g - exact) < 0.06 * exact, (g, exact)
+
+
+def test_statistical_inefficiency_affine_invariant():
+    x = ar1(0.7, 5000, seed=9)
+    g = ostats.statistical_inefficiency(x)
+    assert abs(ostats.statistical_inefficiency(-3.0 * x + 17.0) - g) < 1e-9 * g
+
+
+def test_equilibration_stationary_series_starts_early():
+    x = ar1(0.5, 20_000, seed=11)
+    t0, g, n_eff = ostats.detect_equilibration(x, stride=100)
+    assert t0 <= 0.1 * len(x)
+    assert abs(g - 3.0) < 0.3 and abs(n_eff - (len(x) - t0) / g) < 1e-9
+
+
+def test_equilibration_detects_an_offset_block():
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(10_000)
+    x[:1000] += 3.0                                   # non-equilibrated start
+    t0, g, _ = ostats.detect_equilibration(x, stride=10)
+    assert 990 <= t0 <= 1100, t0
+    assert g < 1.3
+
+
+def test_equilibration_detects_a_relaxation():
+    # exponential relaxation of amplitude 10 on top of AR(1) noise of unit
+    # stationary variance: the transient falls below the noise after
+    # ln(10) * 300 ~ 700 steps; the detected start lies between 2 and 10 decay times
+    n, tau0 = 30_000, 300.0
+    noise = ar1(0.8, n, seed=13) * math.sqrt(1 - 0.64)
+    x = 10.0 * np.exp(-np.arange(n) / tau0) + noise
+    t0, _, _ = ostats.detect_equilibration(x, stride=50)
+    assert 2 * tau0 <= t0 <= 10 * tau0, t0
