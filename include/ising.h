@@ -176,6 +176,22 @@ int ising_binder(const double* moments, int n_sims, double* U);
 int ising_tau_int(const double* x, int64_t n, double c, double* tau, double* tau_err,
                   int64_t* window);
 
+/* Statistical inefficiency of x[0..n-1] (host arrays, n >= 2), after Chodera,
+ * J. Chem. Theory Comput. 12, 1799 (2016): g = 1 + 2 sum_{t>=1} (1 - t/n) C(t)
+ * with C(t) the fluctuation autocorrelation about the series' own mean,
+ * C(t) = [sum_{i<n-t} d_i d_{i+t} / (n - t)] / [sum_i d_i^2 / n], the sum
+ * stopping before the first lag with C(t) <= 0; g >= 1 (1 for a constant
+ * series).  n / g is the number of effectively independent samples. */
+int ising_stat_inefficiency(const double* x, int64_t n, double* g);
+
+/* Automatic equilibration detection (the same reference; the method Section
+ * 3.1 uses to discard non-equilibrated data): over the candidate starts
+ * t = 0, stride, 2 stride, ... <= n - 2, *t0 receives the t that maximises
+ * the effective sample count (n - t) / g(x[t..n-1]) (the smallest such t on
+ * ties), *g and *n_eff (either may be NULL) its g and count.  stride = 0
+ * picks max(1, n / 256).  Host-only; ISING_EINVAL for n < 2 or stride < 0. */
+int ising_equilibration(const double* x, int64_t n, int64_t stride, int64_t* t0, double* g, double* n_eff);
+
 /* Size of a checkpoint of the handle (spins, sweep counter, current E/M,
  * moment sums), and save/load through a host buffer of that size.  Loading
  * into a handle of a different shape is ISING_EINVAL.  Because the generator

@@ -1,8 +1,13 @@
 """Binder-cumulant temperature scan: L in {1024, 2048, 4096} x 16 temperatures
 in [2.20, 2.34] x 3 replicas (144 lattices, 1.06e9 spins) advanced together,
-FP64 moments of m = M/N and e = E/N accumulated on the GPU every sweep, the
-Binder cumulant U = 1 - <m^4>/(3<m^2>^2) per (L, T), and tau_int of |M| and E
-from the per-sweep traces.  Optionally, the learned patch proposal's cost and
+FP64 moments of m = M/N and e = E/N accumulated on the GPU every unit, the
+Binder cumulant U = 1 - <m^4>/(3<m^2>^2) per (L, T), tau_int of |M| and E
+from the per-unit traces, and -- as in the paper's validation (Section 3.1) --
+the non-equilibrated start of each trace found and discarded automatically
+(statistical inefficiency, Chodera 2016) before U is taken again from the
+rest; the crossings of U(T) between lattice sizes estimate T_c.  A unit is a
+checkerboard sweep (--mode plain, the paper's method) or a Swendsen-Wang step
+(--mode cluster).  Optionally, the learned patch proposal's cost and
 acceptance on the same lattices in BF16 and in FP8 (E4M3) inference, with a net
 trained at L = 256 near T_c.
 
@@ -20,42 +25,71 @@ import numpy as np
 from . import ising, workloads
 
 
+def _binder_of(m):
+    m = np.asarray(m, dtype=np.float64)
+    m2 = float(np.mean(m * m))
+    return 1.0 - float(np.mean(m ** 4)) / (3.0 * m2 * m2) if m2 > 0 else float("nan")
+
+
+def _crossing(Ts, Ua, Ub):
+    """Temperature where two U(T) curves cross (linear interpolation between
+    neighbouring temperatures; the first sign change), or None."""
+    d = np.asarray(Ua) - np.asarray(Ub)
+    for i in range(len(Ts) - 1):
+        if d[i] == 0.0:
+            return float(Ts[i])
+        if d[i] * d[i + 1] < 0.0:
+            return float(Ts[i] + (Ts[i + 1] - Ts[i]) * d[i] / (d[i] - d[i + 1]))
+    return None
+
+
 def run(burn: int = 5000, sweeps: int = 50000, learned_rounds: int = 10, seed: int = 77,
-        verbose: bool = True) -> dict:
+        mode: str = "plain", sw_burn: int = 200, verbose: bool = True) -> dict:
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)
     wl = workloads.binder_scan(n_sweeps=sweeps)
-    res = {"lattices": wl.n_sims, "spins": wl.spins, "burn": burn, "sweeps": sweeps}
+    res = {"lattices": wl.n_sims, "spins": wl.spins, "mode": mode, "burn": burn, "sw_burn": sw_burn,
+           "units": sweeps}
     with torch.cuda.stream(stream):
         sim = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=sweeps, stream=stream)
         sim.set_graph(True)
         res["autotune_probe_flip_per_ns"] = sim.autotune(probe_sweeps=10)
         res["plan"] = ising.ising_get_plan(sim.h)
+        if sw_burn > 0:
+            sim.sw_sweep(sw_burn)
         sim.sweep(burn)
         ising.ising_set_measure(sim.h, True)
         ising.ising_reset_moments(sim.h)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         done = 0
-        while done < sweeps:                       # one graph of 1000 sweeps replayed
-            k = min(1000, sweeps - done)
-            sim.sweep(k)
+        chunk = 1000 if mode == "plain" else 100
+        while done < sweeps:                       # one graph per chunk, replayed
+            k = min(chunk, sweeps - done)
+            if mode == "plain":
+                sim.sweep(k)
+            else:
+                sim.sw_sweep(k)
             done += k
         e1.record(stream)
         torch.cuda.synchronize(dev)
         secs = e0.elapsed_time(e1) / 1e3
         res["seconds"] = secs
-        res["flip_per_ns"] = wl.spins * sweeps / (secs * 1e9)
+        res["site_updates_per_ns"] = wl.spins * sweeps / (secs * 1e9)
         mom = ising.ising_moments(sim.h)
         U = ising.ising_binder(mom)
         E, M = sim.trace(sweeps)
     rows = []
     for i, (L, T) in enumerate(zip(wl.Ls, wl.temps)):
-        tm = ising.ising_tau_int(np.abs(M[i]).astype(np.float64))[0]
-        te = ising.ising_tau_int(E[i].astype(np.float64))[0]
-        rows.append({"L": L, "T": T, "U": float(U[i]), "abs_m": float(mom[i, 1] / mom[i, 0]),
-                     "e": float(mom[i, 4] / mom[i, 0]), "tau_absM": tm, "tau_E": te})
+        absm = np.abs(M[i]).astype(np.float64)
+        t0, g, n_eff = ising.ising_equilibration(absm, 0)
+        tm = ising.ising_tau_int(absm[t0:])[0] if len(absm) - t0 >= 2 else float("nan")
+        te = ising.ising_tau_int(E[i][t0:].astype(np.float64))[0] if len(absm) - t0 >= 2 else float("nan")
+        m_eq = M[i][t0:].astype(np.float64) / (L * L)
+        rows.append({"L": L, "T": T, "U_all": float(U[i]), "U": _binder_of(m_eq), "t0": int(t0),
+                     "n_eff": float(n_eff), "abs_m": float(np.abs(m_eq).mean()),
+                     "e": float(E[i][t0:].mean() / (L * L)), "tau_absM": tm, "tau_E": te})
     table = {}
     for r in rows:
         key = (r["L"], round(r["T"], 6))
@@ -64,11 +98,25 @@ def run(burn: int = 5000, sweeps: int = 50000, learned_rounds: int = 10, seed: i
     for (L, T), rs in sorted(table.items()):
         Us = np.array([r["U"] for r in rs])
         summary.append({"L": L, "T": T, "U": float(Us.mean()), "U_err": float(Us.std(ddof=1) / math.sqrt(len(Us))),
+                        "U_all": float(np.mean([r["U_all"] for r in rs])),
+                        "t0": float(np.mean([r["t0"] for r in rs])),
+                        "n_eff": float(np.mean([r["n_eff"] for r in rs])),
                         "abs_m": float(np.mean([r["abs_m"] for r in rs])),
                         "e": float(np.mean([r["e"] for r in rs])),
                         "tau_absM": float(np.mean([r["tau_absM"] for r in rs])),
                         "tau_E": float(np.mean([r["tau_E"] for r in rs]))})
     res["summary"] = summary
+    by_L = {}
+    for r in summary:
+        by_L.setdefault(r["L"], []).append(r)
+    Ls = sorted(by_L)
+    crossings = {}
+    for a in range(len(Ls)):
+        for b in range(a + 1, len(Ls)):
+            ra, rb = by_L[Ls[a]], by_L[Ls[b]]
+            crossings[f"{Ls[a]}/{Ls[b]}"] = _crossing([r["T"] for r in ra], [r["U"] for r in ra],
+                                                      [r["U"] for r in rb])
+    res["U_crossings"] = crossings
     # learned proposal on the same lattices: BF16 vs FP8 inference
     if learned_rounds > 0:
         from .learned_study import default_params
@@ -104,7 +152,7 @@ def run(burn: int = 5000, sweeps: int = 50000, learned_rounds: int = 10, seed: i
                 acc = net.accepted(wl.n_sims)
                 ms = a0.elapsed_time(a1) / learned_rounds
                 res["learned"][name] = {"round_ms": ms, "acceptance": float(acc.sum() / (nwin * learned_rounds)),
-                                        "sweep_equivalents_per_round": ms / (1e3 * secs / sweeps),
+                                        "unit_equivalents_per_round": ms / (1e3 * secs / sweeps),
                                         "patches_per_s": nwin / (ms / 1e3)}
             ising.ising_load(sim.h, state)
             tr.close()
@@ -120,8 +168,12 @@ def main():
     ap.add_argument("--burn", type=int, default=5000)
     ap.add_argument("--sweeps", type=int, default=50000)
     ap.add_argument("--learned-rounds", type=int, default=10)
+    ap.add_argument("--mode", choices=["plain", "cluster"], default="plain",
+                    help="measurement unit: checkerboard sweep or Swendsen-Wang step")
+    ap.add_argument("--sw-burn", type=int, default=200, help="cluster steps before the plain burn-in")
     args = ap.parse_args()
-    run(burn=args.burn, sweeps=args.sweeps, learned_rounds=args.learned_rounds)
+    run(burn=args.burn, sweeps=args.sweeps, learned_rounds=args.learned_rounds, mode=args.mode,
+        sw_burn=args.sw_burn)
 
 
 if __name__ == "__main__":

@@ -1,11 +1,14 @@
 // ising_stats.cpp -- host statistics of Monte Carlo time series: integrated
 // autocorrelation time with the automatic window of Madras and Sokal (J. Stat.
 // Phys. 50, 109 (1988); A. D. Sokal, "Monte Carlo methods in statistical
-// mechanics", 1997), and the Binder cumulant from FP64 moment sums.
+// mechanics", 1997), the Binder cumulant from FP64 moment sums, and the
+// statistical inefficiency with automatic equilibration detection of Chodera
+// (J. Chem. Theory Comput. 12, 1799 (2016)).
 //
 // The paper averages |M| every 10^4-2*10^4 sweeps and discards the
-// non-equilibrated part (Section 3.1); these routines give the error bars and
-// effective sample counts that such averages need.
+// non-equilibrated part with Chodera's method (Section 3.1); these routines
+// give the equilibrated start, error bars and effective sample counts that
+// such averages need.
 #include "../../include/ising.h"
 #include "ising_internal.h"
 
@@ -56,9 +59,68 @@ std::vector<double> autocov_sums(const double* x, int64_t n, double mean) {
     return out;
 }
 
+// Statistical inefficiency g = 1 + 2 sum_{t>=1} (1 - t/n) C(t) of x[0..n-1],
+// C(t) = [sum_{i<n-t} d_i d_{i+t} / (n - t)] / [sum_i d_i^2 / n] about the
+// series' own mean, the sum stopping before the first lag with C(t) <= 0;
+// at least 1.  Lag sums by FFT on long series, one lag at a time otherwise.
+double stat_ineff(const double* x, int64_t n) {
+    double mean = 0.0;
+    for (int64_t i = 0; i < n; ++i) mean += x[i];
+    mean /= (double)n;
+    double var = 0.0;
+    for (int64_t i = 0; i < n; ++i) var += (x[i] - mean) * (x[i] - mean);
+    var /= (double)n;
+    if (!(var > 0.0)) return 1.0;
+    std::vector<double> sums;
+    if (n >= 4096) sums = autocov_sums(x, n, mean);
+    double tau = 0.0;
+    for (int64_t t = 1; t < n; ++t) {
+        double s = 0.0;
+        if (!sums.empty()) {
+            s = sums[(size_t)t];
+        } else {
+            for (int64_t i = 0; i + t < n; ++i) s += (x[i] - mean) * (x[i + t] - mean);
+        }
+        const double C = s / ((double)(n - t) * var);
+        if (!(C > 0.0)) break;
+        tau += (1.0 - (double)t / (double)n) * C;
+    }
+    const double g = 1.0 + 2.0 * tau;
+    return g < 1.0 ? 1.0 : g;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ising_stat_inefficiency(const double* x, int64_t n, double* g) {
+    if (!x || !g) return ising::set_last_error(ISING_EINVAL, "x or g is NULL");
+    if (n < 2) return ising::set_last_error(ISING_EINVAL, "series needs at least 2 points");
+    *g = stat_ineff(x, n);
+    return ISING_OK;
+}
+
+int ising_equilibration(const double* x, int64_t n, int64_t stride, int64_t* t0, double* g, double* n_eff) {
+    if (!x || !t0) return ising::set_last_error(ISING_EINVAL, "x or t0 is NULL");
+    if (n < 2) return ising::set_last_error(ISING_EINVAL, "series needs at least 2 points");
+    if (stride < 0) return ising::set_last_error(ISING_EINVAL, "stride must be >= 0");
+    if (stride == 0) stride = n / 256 > 1 ? n / 256 : 1;
+    double best_n = -1.0, best_g = 1.0;
+    int64_t best_t = 0;
+    for (int64_t s = 0; s <= n - 2; s += stride) {
+        const double gs = stat_ineff(x + s, n - s);
+        const double ns = (double)(n - s) / gs;
+        if (ns > best_n) {
+            best_n = ns;
+            best_g = gs;
+            best_t = s;
+        }
+    }
+    *t0 = best_t;
+    if (g) *g = best_g;
+    if (n_eff) *n_eff = best_n;
+    return ISING_OK;
+}
 
 int ising_tau_int(const double* x, int64_t n, double c, double* tau, double* tau_err, int64_t* window) {
     if (!x || !tau) return ising::set_last_error(ISING_EINVAL, "x or tau is NULL");

@@ -115,6 +115,10 @@ def _load():
                              ctypes.c_int),
             "ising_tau_int": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), i64p], ctypes.c_int),
+            "ising_stat_inefficiency": ([ctypes.POINTER(ctypes.c_double), i64, ctypes.POINTER(ctypes.c_double)],
+                                        ctypes.c_int),
+            "ising_equilibration": ([ctypes.POINTER(ctypes.c_double), i64, i64, i64p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
             "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
@@ -347,6 +351,25 @@ def ising_tau_int(x, c: float = 6.0):
     _check(_load().ising_tau_int(_ptr(a, ctypes.c_double), len(a), c, ctypes.byref(tau), ctypes.byref(err),
                                  ctypes.byref(w)))
     return tau.value, err.value, w.value
+
+
+def ising_stat_inefficiency(x) -> float:
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    g = ctypes.c_double()
+    _check(_load().ising_stat_inefficiency(_ptr(a, ctypes.c_double), len(a), ctypes.byref(g)))
+    return g.value
+
+
+def ising_equilibration(x, stride: int = 0):
+    """(t0, g, n_eff): equilibrated start, its statistical inefficiency and
+    effective sample count."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    t0 = ctypes.c_int64()
+    g = ctypes.c_double()
+    n = ctypes.c_double()
+    _check(_load().ising_equilibration(_ptr(a, ctypes.c_double), len(a), stride, ctypes.byref(t0),
+                                       ctypes.byref(g), ctypes.byref(n)))
+    return t0.value, g.value, n.value
 
 
 ISING_NET_PARAMS = 2945

@@ -132,3 +132,29 @@ def test_equilibration_detects_a_relaxation():
     x = 10.0 * np.exp(-np.arange(n) / tau0) + noise
     t0, _, _ = ostats.detect_equilibration(x, stride=50)
     assert 2 * tau0 <= t0 <= 10 * tau0, t0
+
+
+def test_library_equilibration_matches_oracle():
+    rng = np.random.default_rng(21)
+    cases = []
+    for n, rho, amp, tau0 in [(800, 0.3, 4.0, 50.0), (3000, 0.9, 10.0, 200.0), (6000, 0.7, 5.0, 400.0),
+                              (20_000, 0.95, 8.0, 1500.0), (2000, 0.0, 0.0, 1.0)]:
+        noise = ar1(rho, n, seed=int(rng.integers(1 << 30))) * math.sqrt(1 - rho * rho)
+        cases.append(amp * np.exp(-np.arange(n) / tau0) + noise)
+    step = rng.standard_normal(5000)
+    step[:700] -= 2.5
+    cases.append(step)
+    for x in cases:
+        for stride in (1 if len(x) <= 800 else 0, 37):
+            s = stride or max(1, len(x) // 256)
+            t_ref, g_ref, n_ref = ostats.detect_equilibration(x, s)
+            t_lib, g_lib, n_lib = ising.ising_equilibration(x, stride)
+            assert t_lib == t_ref, (len(x), stride, t_lib, t_ref)
+            assert abs(g_lib - g_ref) < 1e-9 * g_ref and abs(n_lib - n_ref) < 1e-9 * n_ref
+        assert abs(ising.ising_stat_inefficiency(x) - ostats.statistical_inefficiency(x)) < \
+            1e-9 * ostats.statistical_inefficiency(x)
+    assert ising.ising_stat_inefficiency([1.0, 2.0, 3.0, 4.0]) == 1.5
+    with pytest.raises(ising.IsingError):
+        ising.ising_equilibration([1.0], 0)
+    with pytest.raises(ising.IsingError):
+        ising.ising_equilibration([1.0, 2.0, 3.0], -1)
