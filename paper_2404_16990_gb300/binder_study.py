@@ -44,11 +44,11 @@ def _crossing(Ts, Ua, Ub):
 
 
 def run(burn: int = 5000, sweeps: int = 50000, learned_rounds: int = 10, seed: int = 77,
-        mode: str = "plain", sw_burn: int = 200, verbose: bool = True) -> dict:
+        mode: str = "plain", sw_burn: int = 200, t_range=(2.20, 2.34), verbose: bool = True) -> dict:
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)
-    wl = workloads.binder_scan(n_sweeps=sweeps)
+    wl = workloads.binder_scan(n_sweeps=sweeps, t_lo=t_range[0], t_hi=t_range[1])
     res = {"lattices": wl.n_sims, "spins": wl.spins, "mode": mode, "burn": burn, "sw_burn": sw_burn,
            "units": sweeps}
     with torch.cuda.stream(stream):
@@ -171,9 +171,10 @@ def main():
     ap.add_argument("--mode", choices=["plain", "cluster"], default="plain",
                     help="measurement unit: checkerboard sweep or Swendsen-Wang step")
     ap.add_argument("--sw-burn", type=int, default=200, help="cluster steps before the plain burn-in")
+    ap.add_argument("--t-range", type=float, nargs=2, default=[2.20, 2.34], metavar=("T_LO", "T_HI"))
     args = ap.parse_args()
     run(burn=args.burn, sweeps=args.sweeps, learned_rounds=args.learned_rounds, mode=args.mode,
-        sw_burn=args.sw_burn)
+        sw_burn=args.sw_burn, t_range=tuple(args.t_range))
 
 
 if __name__ == "__main__":

@@ -87,13 +87,13 @@ def batch754(n_sweeps: int = 10000, master_seed: int = 20240426) -> Workload:
                     cold=False, n_sweeps=n_sweeps)
 
 
-def binder_scan(n_sweeps: int = 50000) -> Workload:
-    """L in {1024, 2048, 4096} x 16 temperatures in [2.20, 2.34] x 3 replicas
-    (144 lattices)."""
+def binder_scan(n_sweeps: int = 50000, t_lo: float = 2.20, t_hi: float = 2.34) -> Workload:
+    """L in {1024, 2048, 4096} x 16 temperatures in [t_lo, t_hi] (default
+    [2.20, 2.34]) x 3 replicas (144 lattices)."""
     Ls, temps, seeds = [], [], []
     i = 0
     for L in (1024, 2048, 4096):
-        for T in np.linspace(2.20, 2.34, 16):
+        for T in np.linspace(t_lo, t_hi, 16):
             for r in range(3):
                 Ls.append(L)
                 temps.append(float(T))
