@@ -430,6 +430,38 @@ int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes
  * counter are unchanged. */
 int ising_sw_labels(ising_t h, int sim, void* dev_scratch, size_t scratch_bytes, uint32_t* host_labels);
 
+/* ---- Random streams and their quality battery ----------------------------
+ * The paper checks its hardware generator's bit stream with the NIST SP
+ * 800-22 tests and floats shaped from it for uniformity in 100 bins, lag-1
+ * independence and the bits "float >= median" (supplementary, PRNG tests).
+ * These calls give the same checks for the Philox4x32-10 stream this library
+ * draws. */
+
+/* The draws of sites p0 .. p0 + n_p - 1 in sweeps t0 .. t0 + n_t - 1 for key
+ * `seed`, simulation s and phase (0/1 black/white half-sweep, 2 initial
+ * state, 4..8 learned proposal and cluster step), exactly as the kernels use
+ * them: dev_out[(t - t0) * n_p + (p - p0)] = lane p & 3 of the block with
+ * counter (p >> 2, t, s, phase).  dev_out: device memory of n_p * n_t words,
+ * 16-byte aligned, caller-owned.  Needs p0 + n_p <= 2^34 and t0 + n_t <= 2^32
+ * (ISING_EINVAL otherwise).  Asynchronous on cuda_stream. */
+int ising_random_stream(uint64_t seed, uint32_t s, uint32_t phase, uint64_t p0, uint64_t n_p, uint32_t t0,
+                        uint32_t n_t, uint32_t* dev_out, void* cuda_stream);
+
+/* The battery on n_words >= 4096 host words (at most 2^30): the bit stream is
+ * every word most significant bit first, floats are the paper's shaping
+ * (w & 0x7FFFFF) / 2^23.  pvalues[ISING_PRNG_TESTS] (and statistics, if not
+ * NULL) receive, in order: frequency (statistic S = ones - zeros), block
+ * frequency with 128-bit blocks (chi2), runs (number of runs V; p = 0 when the
+ * frequency pre-test fails), longest run of ones in 128-bit blocks in the
+ * classes <= 4, 5, 6, 7, 8, >= 9 with exact class probabilities (chi2),
+ * spectral on the first 2^k <= min(bits, ISING_PRNG_SPECTRAL_MAX_BITS) bits (d),
+ * cumulative sums forward and backward (max excursion z), float uniformity in
+ * 100 bins (chi2), non-overlapping float pairs in a 10 x 10 grid (chi2), and
+ * runs and longest run of the bits "float >= median".  Host-only. */
+#define ISING_PRNG_TESTS 11
+#define ISING_PRNG_SPECTRAL_MAX_BITS (1 << 20)
+int ising_prng_battery(const uint32_t* words, int64_t n_words, double* pvalues, double* statistics);
+
 /* Free the handle (not the workspace).  Synchronises its stream. */
 void ising_destroy(ising_t h);
 

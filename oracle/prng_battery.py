@@ -19,8 +19,10 @@ bit tests.  This module restates those statistics in plain numpy / scipy:
                          probabilities exact from the count of M-bit strings
                          whose longest run is <= k; chi2 over the classes,
                          p = Q(5/2, chi2/2)
-  spectral               X = DFT of 2b - 1; T = sqrt(ln(20) n); N1 = #{|X_k| <
-                         T, k < n/2}; d = (N1 - 0.95 n/2) / sqrt(0.95 * 0.05 n / 4),
+  spectral               on the first n bits, n the largest power of two
+                         <= min(bits, 2^20); X = DFT of 2b - 1;
+                         T = sqrt(ln(20) n); N1 = #{|X_k| < T, k < n/2};
+                         d = (N1 - 0.95 n/2) / sqrt(0.95 * 0.05 n / 4),
                          p = erfc(|d| / sqrt(2))
   cusum(reverse)         z = max |partial sum of 2b - 1|; p from the
                          distribution of the maximum of a random walk's
@@ -115,9 +117,15 @@ def longest_run(b, M: int = 128, lo: int = 4, hi: int = 9):
     return float(special.gammaincc((hi - lo) / 2.0, chi2 / 2.0)), chi2
 
 
+SPECTRAL_MAX_BITS = 1 << 20
+
+
 def spectral(b):
     b = np.asarray(b, dtype=np.float64)
-    n = len(b)
+    n = 1
+    while 2 * n <= min(len(b), SPECTRAL_MAX_BITS):
+        n *= 2
+    b = b[:n]
     X = np.fft.fft(2.0 * b - 1.0)
     mod = np.abs(X[: n // 2])
     T = math.sqrt(math.log(1.0 / 0.05) * n)

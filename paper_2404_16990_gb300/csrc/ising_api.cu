@@ -938,6 +938,18 @@ void ising_destroy(ising_t h) {
 
 }  // extern "C"
 
+extern "C" int ising_random_stream(uint64_t seed, uint32_t s, uint32_t phase, uint64_t p0, uint64_t n_p, uint32_t t0,
+                                   uint32_t n_t, uint32_t* dev_out, void* cuda_stream) {
+    if (!dev_out) return fail(ISING_EINVAL, "dev_out is NULL");
+    if (((uintptr_t)dev_out) % 16 != 0) return fail(ISING_EINVAL, "dev_out must be 16-byte aligned");
+    if (p0 + n_p < p0 || p0 + n_p > (1ull << 34)) return fail(ISING_EINVAL, "sites beyond 2^34");
+    if ((uint64_t)t0 + n_t > (1ull << 32)) return fail(ISING_EINVAL, "sweeps beyond 2^32");
+    if (n_p > 0 && n_t > 0 && n_p > (uint64_t)-1 / n_t) return fail(ISING_EINVAL, "n_p * n_t overflows");
+    CUDA_TRY(launch_random_stream((uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32), s, phase, p0, n_p, t0, n_t,
+                                  dev_out, (cudaStream_t)cuda_stream), "random stream kernel");
+    return ISING_OK;
+}
+
 // ===========================================================================
 // Swendsen-Wang cluster step (kernels in ising_cluster.cu)
 // ===========================================================================

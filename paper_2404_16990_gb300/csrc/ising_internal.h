@@ -135,6 +135,8 @@ cudaError_t launch_stream_persistent(const DevState& st, int n_slats, uint64_t t
                                      cudaStream_t stream);
 int stream_persistent_occupancy(int words_per_thread, int threads);
 cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream);
+cudaError_t launch_random_stream(uint32_t k0, uint32_t k1, uint32_t s, uint32_t phase, uint64_t p0, uint64_t n_p,
+                                 uint32_t t0, uint32_t n_t, uint32_t* out, cudaStream_t stream);
 
 // Record a message for ising_last_error() and return code (ising_api.cu).
 int set_last_error(int code, const char* msg);

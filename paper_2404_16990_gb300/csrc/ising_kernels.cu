@@ -19,6 +19,7 @@
 #include "ising_device.cuh"
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 
 namespace ising {
@@ -535,6 +536,29 @@ __global__ void __launch_bounds__(256, 2) stream_persist_kernel(DevState st, int
 
 __global__ void advance_t_kernel(DevState st, long long n) { st.ctl->t += (unsigned long long)n; }
 
+// The draws of sites p0 .. p0 + n_p - 1 in sweeps t0 .. t0 + n_t - 1, one
+// Philox block per thread: item (t, g) covers the sites of block q = (p0 >> 2)
+// + g that fall inside [p0, p0 + n_p).
+__global__ void __launch_bounds__(256) random_stream_kernel(uint32_t k0, uint32_t k1, uint32_t s, uint32_t phase,
+                                                            unsigned long long p0, unsigned long long n_p,
+                                                            uint32_t t0, uint32_t n_t, unsigned long long blocks,
+                                                            uint32_t* out) {
+    const unsigned long long total = blocks * n_t;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long tt = i / blocks, g = i - tt * blocks;
+        const unsigned long long q = (p0 >> 2) + g;
+        const uint4 r = philox((uint32_t)q, t0 + (uint32_t)tt, s, phase, k0, k1);
+        const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+        uint32_t* row = out + tt * n_p;
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) {
+            const unsigned long long p = 4ull * q + lane;
+            if (p >= p0 && p < p0 + n_p) row[p - p0] = v[lane];
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -671,6 +695,18 @@ cudaError_t launch_stream_persistent(const DevState& st, int n_slats, uint64_t t
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_random_stream(uint32_t k0, uint32_t k1, uint32_t s, uint32_t phase, uint64_t p0, uint64_t n_p,
+                                 uint32_t t0, uint32_t n_t, uint32_t* out, cudaStream_t stream) {
+    if (n_p == 0 || n_t == 0) return cudaSuccess;
+    const uint64_t blocks = ((p0 + n_p + 3) >> 2) - (p0 >> 2);
+    const uint64_t total = blocks * n_t;
+    const uint64_t grid = std::min<uint64_t>((total + 255) / 256, (uint64_t)device_sm_count() * 16);
+    random_stream_kernel<<<(unsigned)grid, 256, 0, stream>>>(k0, k1, s, phase, (unsigned long long)p0,
+                                                             (unsigned long long)n_p, t0, n_t,
+                                                             (unsigned long long)blocks, out);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,10 @@ def _load():
                                         ctypes.c_int),
             "ising_equilibration": ([ctypes.POINTER(ctypes.c_double), i64, i64, i64p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "ising_random_stream": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_uint32, ctypes.c_uint32, vp, vp], ctypes.c_int),
+            "ising_prng_battery": ([ctypes.POINTER(ctypes.c_uint32), i64, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
             "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
@@ -471,6 +475,26 @@ def ising_learned_round(h, net: "IsingNet", round_index: int, sync: bool = True)
     acc = np.zeros(max(1, n), dtype=np.int64)
     _check(_load().ising_learned_round(h, net.h, round_index, _ptr(acc, ctypes.c_int64)))
     return acc[:n]
+
+
+ISING_PRNG_TESTS = 11
+PRNG_TEST_NAMES = ("frequency", "block_frequency", "runs", "longest_run", "spectral", "cusum_forward",
+                   "cusum_backward", "float_uniformity", "float_pairs", "median_runs", "median_longest_run")
+
+
+def ising_random_stream(seed: int, s: int, phase: int, p0: int, n_p: int, t0: int, n_t: int, dev_out: int,
+                        cuda_stream: int = 0) -> None:
+    _check(_load().ising_random_stream(seed, s, phase, p0, n_p, t0, n_t, dev_out, cuda_stream))
+
+
+def ising_prng_battery(words):
+    """(p-values, statistics) of the eleven battery tests on host words."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    p = np.zeros(ISING_PRNG_TESTS)
+    st = np.zeros(ISING_PRNG_TESTS)
+    _check(_load().ising_prng_battery(_ptr(w, ctypes.c_uint32), len(w), _ptr(p, ctypes.c_double),
+                                      _ptr(st, ctypes.c_double)))
+    return p, st
 
 
 def ising_sw_scratch_bytes(h) -> int:

@@ -102,3 +102,36 @@ def test_cusum_pvalue_matches_monte_carlo_tail():
         emp = float((zmax >= z).mean())
         se = math.sqrt(emp * (1 - emp) / reps)
         assert abs(p - emp) < 4 * se + 0.01, (z, p, emp)
+
+
+# --------------------------------------------------------------------------
+# The library's host battery (C ABI) against the oracle.
+# --------------------------------------------------------------------------
+def _philox_words(seed, s, t, phase, n_words):
+    import oracle
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    out = np.empty(n_words, dtype=np.uint32)
+    for q in range(n_words // 4):
+        out[4 * q:4 * q + 4] = oracle.philox4x32_10([q, t, s, phase], key)
+    return out
+
+
+def test_library_battery_matches_oracle():
+    from paper_2404_16990_gb300 import ising
+    rng = np.random.default_rng(77)
+    streams = [rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32) for n in (4096, 5000, 40_000)]
+    streams.append(_philox_words(2, 0, 0, 0, 1 << 14))
+    streams.append(np.full(4096, 0x55555555, dtype=np.uint32))          # a failing stream: runs pre-test passes
+    biased = (rng.random((4096, 32)) < 0.6).astype(np.uint64)
+    streams.append((biased << np.arange(31, -1, -1, dtype=np.uint64)).sum(axis=1).astype(np.uint32))
+    for w in streams:
+        p_ref, s_ref = pb.battery(w)
+        p_lib, s_lib = ising.ising_prng_battery(w)
+        for j, name in enumerate(pb.TESTS):
+            if np.isnan(s_ref[j]):
+                assert np.isnan(s_lib[j]) and p_lib[j] == p_ref[j] == 0.0, name
+                continue
+            assert abs(s_lib[j] - s_ref[j]) <= 1e-9 * max(1.0, abs(s_ref[j])), (name, len(w), s_lib[j], s_ref[j])
+            assert abs(p_lib[j] - p_ref[j]) <= 1e-9 + 1e-7 * p_ref[j], (name, len(w), p_lib[j], p_ref[j])
+    with pytest.raises(ising.IsingError):
+        ising.ising_prng_battery(np.zeros(4095, dtype=np.uint32))
