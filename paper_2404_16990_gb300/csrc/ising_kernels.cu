@@ -53,6 +53,18 @@ struct SiteKey {
     uint32_t t, s, phase, k0, k1, thr0, thr1;
 };
 
+// 2 acc + [r >= t]: sub.cc leaves the carry of r + ~t + 1, which is 1 exactly
+// when r >= t (no borrow), and addc adds it to acc + acc -- two carry-chain
+// instructions shift one comparison result into a word.
+__device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t r, uint32_t t) {
+    uint32_t diff, out;
+    asm("sub.cc.u32 %0, %2, %3;\n\t"
+        "addc.u32 %1, %4, %4;"
+        : "=r"(diff), "=r"(out)
+        : "r"(r), "r"(t), "r"(acc));
+    return out;
+}
+
 __device__ __forceinline__ uint32_t metropolis_word(uint32_t w, uint32_t up, uint32_t dn,
                                                     uint32_t same, uint32_t side, uint32_t q0,
                                                     const SiteKey& key) {
@@ -66,24 +78,23 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t w, uint32_t up, uin
     const uint32_t b2 = c1 & c2;                    // fours of a (a == 4)
     const uint32_t need8 = b2;
     const uint32_t need4 = b0 & b1;                 // a == 3
-    uint32_t flip = ~(need4 | need8);
-    // per-site threshold: thr0 ^ (dx & -bit) picks thr1 where need8 is set,
-    // without a branch or a predicate select
-    const uint32_t dx = key.thr0 ^ key.thr1;
+    // every draw against both thresholds: the bits [r >= thr0] and [r >= thr1]
+    // are shifted into two words from site 31 down to site 0, so bit k ends
+    // up at site k, with no per-site threshold select
+    uint32_t ge0 = 0, ge1 = 0;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
+    for (int g = 7; g >= 0; --g) {
         const uint4 r = philox(q0 + (uint32_t)g, key.t, key.s, key.phase, key.k0, key.k1);
-        const uint32_t n8 = need8 >> (4 * g);
-        const uint32_t t0 = key.thr0 ^ (dx & (0u - (n8 & 1u)));
-        const uint32_t t1 = key.thr0 ^ (dx & (0u - ((n8 >> 1) & 1u)));
-        const uint32_t t2 = key.thr0 ^ (dx & (0u - ((n8 >> 2) & 1u)));
-        const uint32_t t3 = key.thr0 ^ (dx & (0u - ((n8 >> 3) & 1u)));
-        if (r.x < t0) flip |= 1u << (4 * g + 0);
-        if (r.y < t1) flip |= 1u << (4 * g + 1);
-        if (r.z < t2) flip |= 1u << (4 * g + 2);
-        if (r.w < t3) flip |= 1u << (4 * g + 3);
+        ge0 = shift_in_not_below(ge0, r.w, key.thr0);
+        ge1 = shift_in_not_below(ge1, r.w, key.thr1);
+        ge0 = shift_in_not_below(ge0, r.z, key.thr0);
+        ge1 = shift_in_not_below(ge1, r.z, key.thr1);
+        ge0 = shift_in_not_below(ge0, r.y, key.thr0);
+        ge1 = shift_in_not_below(ge1, r.y, key.thr1);
+        ge0 = shift_in_not_below(ge0, r.x, key.thr0);
+        ge1 = shift_in_not_below(ge1, r.x, key.thr1);
     }
-    return w ^ flip;
+    return w ^ (~(need4 | need8) | (need4 & ~ge0) | (need8 & ~ge1));
 }
 
 // Horizontal neighbour word: for bit b the site j+1 (plus) or j-1 (minus) of
