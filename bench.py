@@ -35,7 +35,7 @@ SM_MAX_MHZ = 2070.0
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch, from the committed ncu summary
 # profiles/stream_half_kernel_L16384x6.md (full capture, launch 1)
-MEASURED_TRAFFIC = {("l16384", "stream_half_kernel", 3 * 16384 * 16384 // 2): 110_603_776}
+MEASURED_TRAFFIC = {("l16384", "stream_half_kernel", 3 * 16384 * 16384 // 2): 110_947_840}
 
 
 def parse():

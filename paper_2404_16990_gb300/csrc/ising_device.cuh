@@ -26,8 +26,10 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     for (int r = 0; r < 10; ++r) {
         const uint32_t ka = k0 + (uint32_t)r * kWeylA;
         const uint32_t kb = k1 + (uint32_t)r * kWeylB;
-        const uint32_t hi_a = __umulhi(kMulA, c0), lo_a = kMulA * c0;
-        const uint32_t hi_b = __umulhi(kMulB, c2), lo_b = kMulB * c2;
+        // one 32x32->64 product each (a single wide multiply-add instruction)
+        const uint64_t pa = (uint64_t)kMulA * c0, pb = (uint64_t)kMulB * c2;
+        const uint32_t hi_a = (uint32_t)(pa >> 32), lo_a = (uint32_t)pa;
+        const uint32_t hi_b = (uint32_t)(pb >> 32), lo_b = (uint32_t)pb;
         c0 = hi_b ^ c1 ^ ka;
         c1 = lo_b;
         c2 = hi_a ^ c3 ^ kb;
