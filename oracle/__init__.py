@@ -9,7 +9,8 @@ method's arithmetic) serve both sides.
 
 The arithmetic lives in ``ising_oracle.c`` (plain C, one byte per spin, the
 definitions of Section 1 and Algorithm 5 written out site by site) and
-``cluster_oracle.c`` (the Swendsen-Wang cluster step named in Section 1);
+``cluster_oracle.c`` (the Swendsen-Wang cluster step named in Section 1) and
+``ising3d_oracle.c`` (the same sweep on the simple cubic lattice);
 this module compiles them with gcc and wraps them with ctypes and numpy.
 """
 from __future__ import annotations
@@ -23,7 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
-_SOURCES = ("ising_oracle.c", "cluster_oracle.c")
+_SOURCES = ("ising_oracle.c", "cluster_oracle.c", "ising3d_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +112,21 @@ def _load():
                                                ctypes.c_uint32, ctypes.c_int64, i64p, i64p,
                                                ctypes.c_int]
         lib.oracle_sw_sweeps_batch.restype = ctypes.c_int
+        lib.oracle3d_thresholds.argtypes = [ctypes.c_double, u32p]
+        lib.oracle3d_thresholds.restype = ctypes.c_int
+        lib.oracle3d_init.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i8p]
+        lib.oracle3d_init.restype = ctypes.c_int
+        lib.oracle3d_energy.argtypes = [ctypes.c_int, i8p]
+        lib.oracle3d_energy.restype = ctypes.c_int64
+        lib.oracle3d_magnetization.argtypes = [ctypes.c_int, i8p]
+        lib.oracle3d_magnetization.restype = ctypes.c_int64
+        lib.oracle3d_sweeps.argtypes = [ctypes.c_int, i8p, u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_int64, i64p, i64p]
+        lib.oracle3d_sweeps.restype = None
+        lib.oracle3d_sweeps_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i8p), u32p,
+                                              ctypes.POINTER(ctypes.c_uint64), u32p, ctypes.c_uint32,
+                                              ctypes.c_int64, i64p, i64p, ctypes.c_int]
+        lib.oracle3d_sweeps_batch.restype = None
         _lib = lib
         return lib
 
@@ -290,6 +306,62 @@ def sw_sweeps_batch(sigmas, temps, seeds, sims, t0: int, n: int, n_threads: int 
                                             max(1, n_threads))
     if failed:
         raise MemoryError("oracle_sw_sweeps_batch: allocation failed")
+    return E, M
+
+
+# --- three-dimensional sweep (ising3d_oracle.c) ------------------------------
+
+def thresholds3d(T: float) -> np.ndarray:
+    """u32 thresholds [dE = 4, 8, 12] at temperature T."""
+    thr = np.zeros(3, dtype=np.uint32)
+    if _load().oracle3d_thresholds(float(T), _ptr(thr, ctypes.c_uint32)) != 0:
+        raise ValueError(f"invalid temperature {T!r}")
+    return thr
+
+
+def init3d(L: int, seed: int, s: int = 0, cold: bool = False) -> np.ndarray:
+    sigma = np.empty((L, L, L), dtype=np.int8)          # [z, y, x]
+    if _load().oracle3d_init(L, seed, s, 1 if cold else 0, _ptr(sigma, ctypes.c_int8)) != 0:
+        raise ValueError(f"invalid L {L}")
+    return sigma
+
+
+def energy3d(sigma: np.ndarray) -> int:
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    return int(_load().oracle3d_energy(sigma.shape[0], _ptr(sigma, ctypes.c_int8)))
+
+
+def magnetization3d(sigma: np.ndarray) -> int:
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    return int(_load().oracle3d_magnetization(sigma.shape[0], _ptr(sigma, ctypes.c_int8)))
+
+
+def sweeps3d(sigma: np.ndarray, T: float, seed: int, s: int, t0: int, n: int):
+    """In place: n sweeps of an L^3 lattice [z, y, x] from sweep index t0."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    E = np.zeros(max(n, 0), dtype=np.int64)
+    M = np.zeros(max(n, 0), dtype=np.int64)
+    thr = thresholds3d(T)
+    _load().oracle3d_sweeps(sigma.shape[0], _ptr(sigma, ctypes.c_int8), _ptr(thr, ctypes.c_uint32), seed, s, t0, n,
+                            _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64))
+    return E, M
+
+
+def sweeps3d_batch(sigmas, temps, seeds, sims, t0: int, n: int, n_threads: int = 1):
+    n_lat = len(sigmas)
+    Ls = np.array([x.shape[0] for x in sigmas], dtype=np.int32)
+    thr = np.concatenate([thresholds3d(T) for T in temps]).astype(np.uint32) if n_lat else np.zeros(0, np.uint32)
+    seeds_a = np.array([int(x) for x in seeds], dtype=np.uint64)
+    sims_a = np.array([int(x) for x in sims], dtype=np.uint32)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * max(n_lat, 1))()
+    for j, x in enumerate(sigmas):
+        assert x.dtype == np.int8 and x.flags.c_contiguous
+        ptrs[j] = _ptr(x, ctypes.c_int8)
+    E = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    M = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    _load().oracle3d_sweeps_batch(n_lat, _ptr(Ls, ctypes.c_int), ptrs, _ptr(thr, ctypes.c_uint32),
+                                  _ptr(seeds_a, ctypes.c_uint64), _ptr(sims_a, ctypes.c_uint32), t0, n,
+                                  _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), max(1, n_threads))
     return E, M
 
 

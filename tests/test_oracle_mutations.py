@@ -108,3 +108,52 @@ def test_sw_unmodified_source_passes_same_checks(tmp_path):
     so = oracle.compile_variant(oracle.source_text("cluster_oracle.c"), str(tmp_path), "sw_clean",
                                 which="cluster_oracle.c")
     assert _caught_sw(so) == []
+
+
+# --------------------------------------------------------------------------
+# The same for the three-dimensional oracle (ising3d_oracle.c).
+# --------------------------------------------------------------------------
+import test_ising3d_oracle as pins3d  # noqa: E402
+
+MUTATIONS_3D = {
+    "3d_dropped_neighbour": ("sigma[at3(L, x, y, z - 1)] + sigma[at3(L, x, y, z + 1)];",
+                             "sigma[at3(L, x, y, z + 1)];"),
+    "3d_threshold_index": ("< thr[dE / 4 - 1];", "< thr[dE / 4 - 1 > 0 ? dE / 4 - 2 : 0];"),
+    "3d_colour_rule": ("if (((x + y + z) & 1) != c) continue;", "if (((x + y) & 1) != c) continue;"),
+    "3d_energy_missing_axis": ("sigma[at3(L, x + 1, y, z)] + sigma[at3(L, x, y + 1, z)] + sigma[at3(L, x, y, z + 1)];",
+                               "sigma[at3(L, x + 1, y, z)] + sigma[at3(L, x, y + 1, z)];"),
+}
+
+
+def _caught_3d(variant_so) -> list:
+    caught = []
+    with oracle.use_library(variant_so):
+        checks = [
+            ("closed_forms", lambda: pins3d.test_energy3d_closed_forms(4)),
+            ("chi2_2x2x2", lambda: pins3d.test_2x2x2_joint_distribution_matches_enumeration(4.5)),
+            ("chi2_2x2x2_cold", lambda: pins3d.test_2x2x2_joint_distribution_matches_enumeration(2.0)),
+            ("series", pins3d.test_high_temperature_series3d),
+            ("t0", pins3d.test_zero_temperature3d),
+            ("t0_neel", pins3d.test_zero_temperature_neel_worked_case),
+        ]
+        for name, fn in checks:
+            try:
+                fn()
+            except AssertionError:
+                caught.append(name)
+    return caught
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_3D))
+def test_3d_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS_3D[name]
+    src = oracle.source_text("ising3d_oracle.c")
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    so = oracle.compile_variant(src.replace(old, new), str(tmp_path), "o3d_" + name, which="ising3d_oracle.c")
+    assert _caught_3d(so), f"no pin caught the planted mistake {name}"
+
+
+def test_3d_unmodified_source_passes_same_checks(tmp_path):
+    so = oracle.compile_variant(oracle.source_text("ising3d_oracle.c"), str(tmp_path), "o3d_clean",
+                                which="ising3d_oracle.c")
+    assert _caught_3d(so) == []
