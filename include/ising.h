@@ -462,6 +462,36 @@ int ising_random_stream(uint64_t seed, uint32_t s, uint32_t phase, uint64_t p0, 
 #define ISING_PRNG_SPECTRAL_MAX_BITS (1 << 20)
 int ising_prng_battery(const uint32_t* words, int64_t n_words, double* pvalues, double* statistics);
 
+/* ---- The three-dimensional sweep -----------------------------------------
+ * The paper's Hamiltonian (Section 1) for the simple cubic lattice: periodic
+ * L x L x L, J = 1, h = 0, six nearest neighbours; the checkerboard sweep of
+ * Algorithm 5 with colours (x + y + z) & 1 (0 = black first).  A site flips
+ * iff dE <= 0 or r < thr[dE/4 - 1], thr = min(floor(2^32 exp(-dE/T)),
+ * 2^32 - 1) for dE = 4, 8, 12.  Layout: word[((c L + z) L + y) (L/64) + k],
+ * bit b <-> x = 2 (32 k + b) + ((y + z + c) & 1), bit 1 = spin -1.  Draws:
+ * Philox4x32-10, key (lo32, hi32 of seeds[i]), counter (p >> 2, t, i, phase),
+ * lane p & 3, p = (z L + y) (L/2) + (x >> 1) in the half-sweeps (phase 0/1)
+ * and p = (z L + y) L + x for the random start (phase 2, +1 iff the top bit
+ * is 0).  E = -sum over bonds, M = sum of spins, exact 64-bit integers.
+ * Sides: multiples of 64 in [64, ISING3D_MAX_L].  Conventions (errors,
+ * ownership, streams) as for the 2D calls above. */
+#define ISING3D_MAX_L 1024
+typedef struct ising3d_handle* ising3d_t;
+int ising3d_workspace_bytes(int n_sims, const int* Ls, int64_t trace_cap, size_t* bytes);
+int ising3d_create(ising3d_t* out, int n_sims, const int* Ls, const double* temps, const uint64_t* seeds, int init,
+                   int64_t trace_cap, void* dev_workspace, size_t ws_bytes, void* cuda_stream);
+/* n sweeps (black then white half-sweep, then E and M into the trace ring);
+ * asynchronous; graph replay per n when ising3d_set_graph is on. */
+int ising3d_sweep(ising3d_t h, int64_t n);
+int ising3d_set_graph(ising3d_t h, int on);
+int64_t ising3d_sweeps_done(ising3d_t h);
+int64_t ising3d_kernel_launches(ising3d_t h);
+int ising3d_observables(ising3d_t h, int64_t* E, int64_t* M);
+int ising3d_trace(ising3d_t h, int64_t* E, int64_t* M, int64_t max_sweeps, int64_t* n_out);
+/* Unpacked spins of lattice sim, host_LLL[(z L + y) L + x] in {+1, -1}. */
+int ising3d_get_spins(ising3d_t h, int sim, int8_t* host_LLL);
+void ising3d_destroy(ising3d_t h);
+
 /* Free the handle (not the workspace).  Synchronises its stream. */
 void ising_destroy(ising_t h);
 

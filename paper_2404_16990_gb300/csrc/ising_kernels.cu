@@ -62,6 +62,7 @@ __device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t r,
         "addc.u32 %1, %4, %4;"
         : "=r"(diff), "=r"(out)
         : "r"(r), "r"(t), "r"(acc));
+    (void)diff;
     return out;
 }
 

@@ -123,6 +123,18 @@ def _load():
                                      ctypes.c_uint32, ctypes.c_uint32, vp, vp], ctypes.c_int),
             "ising_prng_battery": ([ctypes.POINTER(ctypes.c_uint32), i64, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "ising3d_workspace_bytes": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64, ctypes.POINTER(sz)], ctypes.c_int),
+            "ising3d_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, i64,
+                                vp, sz, vp], ctypes.c_int),
+            "ising3d_sweep": ([vp, i64], ctypes.c_int),
+            "ising3d_set_graph": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising3d_sweeps_done": ([vp], i64),
+            "ising3d_kernel_launches": ([vp], i64),
+            "ising3d_observables": ([vp, i64p, i64p], ctypes.c_int),
+            "ising3d_trace": ([vp, i64p, i64p, i64, i64p], ctypes.c_int),
+            "ising3d_get_spins": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)], ctypes.c_int),
+            "ising3d_destroy": ([vp], None),
             "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
             "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
@@ -613,6 +625,77 @@ class IsingSim:
     def close(self) -> None:
         if getattr(self, "h", None):
             ising_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class IsingSim3D:
+    """Owner of one three-dimensional handle (lattices of side Ls[i], L^3
+    spins each) and its torch-allocated device workspace."""
+
+    def __init__(self, Ls: Sequence[int], temps: Sequence[float], seeds: Sequence[int], *, cold: bool = False,
+                 trace_cap: int = 0, stream=None, device=None):
+        import torch
+        self._torch = torch
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        lib = _load()
+        self.Ls = [int(L) for L in Ls]
+        n = len(self.Ls)
+        Ls_a = np.array(self.Ls, dtype=np.int32)
+        T_a = np.array(list(temps), dtype=np.float64)
+        S_a = np.array([int(x) for x in seeds], dtype=np.uint64)
+        nbytes = ctypes.c_size_t()
+        _check(lib.ising3d_workspace_bytes(n, _ptr(Ls_a, ctypes.c_int), trace_cap, ctypes.byref(nbytes)))
+        with torch.cuda.device(device):
+            self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        _check(lib.ising3d_create(ctypes.byref(h), n, _ptr(Ls_a, ctypes.c_int), _ptr(T_a, ctypes.c_double),
+                                  _ptr(S_a, ctypes.c_uint64), ISING_INIT_COLD if cold else ISING_INIT_RANDOM,
+                                  trace_cap, self.workspace.data_ptr(), nbytes.value, self.stream.cuda_stream))
+        self.h = h.value
+        self.n = n
+
+    def sweep(self, n: int) -> None:
+        _check(_load().ising3d_sweep(self.h, n))
+
+    def set_graph(self, on: bool) -> None:
+        _check(_load().ising3d_set_graph(self.h, 1 if on else 0))
+
+    @property
+    def sweeps_done(self) -> int:
+        return int(_load().ising3d_sweeps_done(self.h))
+
+    def observables(self):
+        E = np.zeros(self.n, dtype=np.int64)
+        M = np.zeros(self.n, dtype=np.int64)
+        _check(_load().ising3d_observables(self.h, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64)))
+        return E, M
+
+    def trace(self, max_sweeps: int):
+        E = np.zeros((self.n, max(1, max_sweeps)), dtype=np.int64)
+        M = np.zeros_like(E)
+        k = ctypes.c_int64()
+        _check(_load().ising3d_trace(self.h, _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), max_sweeps,
+                                     ctypes.byref(k)))
+        return E.reshape(-1)[: self.n * k.value].reshape(self.n, k.value), \
+            M.reshape(-1)[: self.n * k.value].reshape(self.n, k.value)
+
+    def spins(self, sim: int = 0) -> np.ndarray:
+        L = self.Ls[sim]
+        out = np.zeros((L, L, L), dtype=np.int8)
+        _check(_load().ising3d_get_spins(self.h, sim, _ptr(out, ctypes.c_int8)))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _load().ising3d_destroy(self.h)
             self.h = None
 
     def __del__(self):
