@@ -28,14 +28,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 T_RUNS = (1.5, 2.269185, 3.0)
-OPS_PER_SITE = 18.5   # algorithmic integer ops per site update (derivation in the design doc)
+# algorithmic integer ops per site update: a quarter Philox4x32-10 block (15),
+# the accept decision (3), the bitsliced neighbour count (0.5)
+OPS_PER_SITE = 18.5
 SMS = 152
 INT_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch, from the committed ncu summary
-# profiles/stream_half_kernel_L16384x6.md (full capture, launch 1)
-MEASURED_TRAFFIC = {("l16384", "stream_half_kernel", 3 * 16384 * 16384 // 2): 110_947_840}
+# dram__bytes_write.sum of one launch of that kernel build, from an ncu full
+# capture (first captured launch); other pairings report null
+MEASURED_TRAFFIC = {("l16384", "stream_half_kernel<4>", 3 * 16384 * 16384 // 2): 110_620_416}
 
 
 def parse():
@@ -280,12 +282,13 @@ def ours(args):
     # kernel or the resident kernel (one launch per sweep call per handle);
     # either way the algorithmic ops of the timed region over its duration
     plan = ising.ising_get_plan(sims[0].h)
+    V = plan["words_per_thread"]
     if plan["plan"] == ising.ISING_PLAN_RESIDENT:
         kname, n_launch = "resident_kernel", len(sims) * args.steps
     elif plan["plan"] == ising.ISING_PLAN_PERSIST:
-        kname, n_launch = "stream_persist_kernel", len(sims) * args.steps
+        kname, n_launch = f"stream_persist_kernel<{V}>", len(sims) * args.steps
     else:
-        kname, n_launch = "stream_half_kernel", 2 * n_sw * len(sims) * args.steps
+        kname, n_launch = f"stream_half_kernel<{V}>", 2 * n_sw * len(sims) * args.steps
     avg_launch_s = (sum(step_ms) / 1e3) / n_launch
     sites_per_launch = flips_per_step * args.steps / n_launch
     achieved = OPS_PER_SITE * sites_per_launch / avg_launch_s / 1e12

@@ -253,7 +253,10 @@ int build_tables(ising_handle* h) {
 
     // streamed lattices: tiles of (tw word groups) x (th row groups of R rows)
     std::vector<StreamLat> slats;
-    int V = h->plan.words_per_thread > 0 ? h->plan.words_per_thread : 2;
+    // default: 4 words (128 sites) per thread and row, halved while a
+    // streamed lattice's row does not divide (the fastest tiling measured on
+    // large lattices)
+    int V = h->plan.words_per_thread > 0 ? h->plan.words_per_thread : 4;
     for (int i : streamed)
         while (V > 1 && (h->L[i] / 64) % V != 0) V /= 2;
     h->V = V;
