@@ -116,38 +116,58 @@ __device__ __forceinline__ Words6 load6(const uint32_t* base, uint32_t L, uint32
     return r;
 }
 
-// One half-sweep of colour c over every lattice: one thread per word.
+// One half-sweep of colour c over every lattice: one thread per V consecutive
+// words of a row (the x neighbours of inner words come from the thread's own
+// loads).
+template <int V>
 __global__ void __launch_bounds__(256) half3d_kernel(State3 st, uint32_t c) {
     const uint32_t t = (uint32_t)st.ctl->t;
-    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < st.items;
+    const uint64_t groups = st.items / V;
+    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < groups;
          item += (uint64_t)gridDim.x * blockDim.x) {
-        const Lat3 d = st.lat[lattice_of_item(st.lat, st.n, item)];
+        const Lat3 d = st.lat[lattice_of_item(st.lat, st.n, item * V)];
         const uint32_t L = d.L, wn = d.wn;
-        const uint64_t i = item - d.item_begin;
-        const uint32_t k = (uint32_t)(i % wn);
+        const uint64_t i = item * V - d.item_begin;
+        const uint32_t k0 = (uint32_t)(i % wn);
         const uint32_t y = (uint32_t)((i / wn) % L), z = (uint32_t)(i / ((uint64_t)wn * L));
         uint32_t* base = st.spins + d.word_off;
-        const Words6 v = load6(base, L, wn, c, z, y, k);
-        const uint32_t w = v.w;
-        uint32_t b0, b1, b2;
-        count6(~(w ^ v.yl), ~(w ^ v.yh), ~(w ^ v.zl), ~(w ^ v.zh), ~(w ^ v.same), ~(w ^ v.side), b0, b1, b2);
-        const uint32_t needA = b2 & ~b1 & ~b0, needB = b2 & ~b1 & b0, needC = b2 & b1;   // a = 4, 5, 6
-        const uint32_t q0 = ((z * L + y) * (L / 2) + 32u * k) >> 2;
-        // [r >= thr] shifted in from site 31 down to site 0 (as in the 2D sweep)
-        uint32_t ge0 = 0, ge1 = 0, ge2 = 0;
+        const uint32_t o = c ^ 1u;
+        const uint32_t ym = (y == 0) ? L - 1 : y - 1, yp = (y + 1 == L) ? 0 : y + 1;
+        const uint32_t zm = (z == 0) ? L - 1 : z - 1, zp = (z + 1 == L) ? 0 : z + 1;
+        auto row = [&](uint32_t cc, uint32_t zz, uint32_t yy) { return base + (((size_t)cc * L + zz) * L + yy) * wn; };
+        uint32_t* own = row(c, z, y);
+        const uint32_t *sm = row(o, z, y), *yl = row(o, z, ym), *yh = row(o, z, yp), *zl = row(o, zm, y), *zh = row(o, zp, y);
+        const bool plus = ((y + z + c) & 1u) != 0;
+        const uint32_t kk = plus ? ((k0 + V == wn) ? 0 : k0 + V) : ((k0 == 0) ? wn - 1 : k0 - 1);
+        const uint32_t nb = sm[kk];
+        uint32_t same[V];
 #pragma unroll
-        for (int g = 7; g >= 0; --g) {
-            const uint4 r = philox(q0 + (uint32_t)g, t, d.sim, c, d.key0, d.key1);
-            const uint32_t rr[4] = {r.w, r.z, r.y, r.x};
+        for (int v = 0; v < V; ++v) same[v] = sm[k0 + v];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                ge0 = shift_in_not_below3(ge0, rr[l], d.thr[0]);
-                ge1 = shift_in_not_below3(ge1, rr[l], d.thr[1]);
-                ge2 = shift_in_not_below3(ge2, rr[l], d.thr[2]);
+        for (int v = 0; v < V; ++v) {
+            const uint32_t k = k0 + v;
+            const uint32_t w = own[k];
+            const uint32_t adj = plus ? ((v + 1 < V) ? same[(v + 1) % V] : nb) : ((v > 0) ? same[(v + V - 1) % V] : nb);
+            const uint32_t side = plus ? __funnelshift_r(same[v], adj, 1) : __funnelshift_l(adj, same[v], 1);
+            uint32_t b0, b1, b2;
+            count6(~(w ^ yl[k]), ~(w ^ yh[k]), ~(w ^ zl[k]), ~(w ^ zh[k]), ~(w ^ same[v]), ~(w ^ side), b0, b1, b2);
+            const uint32_t needA = b2 & ~b1 & ~b0, needB = b2 & ~b1 & b0, needC = b2 & b1;   // a = 4, 5, 6
+            const uint32_t q0 = ((z * L + y) * (L / 2) + 32u * k) >> 2;
+            // [r >= thr] shifted in from site 31 down to site 0 (as in the 2D sweep)
+            uint32_t ge0 = 0, ge1 = 0, ge2 = 0;
+#pragma unroll
+            for (int g = 7; g >= 0; --g) {
+                const uint4 r = philox(q0 + (uint32_t)g, t, d.sim, c, d.key0, d.key1);
+                const uint32_t rr[4] = {r.w, r.z, r.y, r.x};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    ge0 = shift_in_not_below3(ge0, rr[l], d.thr[0]);
+                    ge1 = shift_in_not_below3(ge1, rr[l], d.thr[1]);
+                    ge2 = shift_in_not_below3(ge2, rr[l], d.thr[2]);
+                }
             }
+            own[k] = w ^ (~b2 | (needA & ~ge0) | (needB & ~ge1) | (needC & ~ge2));
         }
-        const uint32_t flip = ~b2 | (needA & ~ge0) | (needB & ~ge1) | (needC & ~ge2);
-        base[(((size_t)c * L + z) * L + y) * wn + k] = w ^ flip;
     }
 }
 
@@ -299,6 +319,7 @@ struct ising3d_handle {
     char* ws = nullptr;
     Layout3 layout;
     State3 st{};
+    int V = 1;
     bool graph = false;
     std::map<int64_t, cudaGraphExec_t> graphs;
     int grid = 0;
@@ -327,7 +348,11 @@ int enqueue_obs3(ising3d_handle* h, int advance) {
 int enqueue_sweeps3(ising3d_handle* h, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         for (uint32_t c = 0; c < 2; ++c) {
-            half3d_kernel<<<h->grid, 256, 0, h->stream>>>(h->st, c);
+            switch (h->V) {
+            case 4: half3d_kernel<4><<<h->grid, 256, 0, h->stream>>>(h->st, c); break;
+            case 2: half3d_kernel<2><<<h->grid, 256, 0, h->stream>>>(h->st, c); break;
+            default: half3d_kernel<1><<<h->grid, 256, 0, h->stream>>>(h->st, c); break;
+            }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail3(e, "3d half-sweep");
         }
@@ -400,7 +425,12 @@ int ising3d_create(ising3d_t* out, int n_sims, const int* Ls, const double* temp
     Ctl3 ctl{};
     ctl.trace_cap = trace_cap;
     int sms = device_sm_count();
-    h->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)sms * 8));
+    // words per thread: 2 (the fastest measured on 512^3 and 1024^3), or 1
+    // when some row has an odd number of words
+    h->V = 2;
+    for (int i = 0; i < n_sims; ++i)
+        if ((Ls[i] / 64) % 2 != 0) h->V = 1;
+    h->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((items / h->V + 255) / 256, (uint64_t)sms * 8));
     cudaError_t e = cudaMemsetAsync(h->ws, 0, lay.spins, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->ws + lay.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
