@@ -1205,7 +1205,7 @@ int net_refresh_fp8(ising_net* net) {
 
 cudaError_t net_score(ising_net* net, const int8_t* win, int n, float* lq, float* z, cudaStream_t st) {
     if (net->precision == ISING_NET_FP8) return launch_net_forward_fp8(net->ns, win, n, lq, z, st);
-    return launch_net_forward(net->ns, win, n, lq, z, nullptr, st);
+    return launch_net_score(net->ns, win, n, lq, z, nullptr, nullptr, st);   // all positions at once
 }
 
 cudaError_t net_sample(ising_net* net, int8_t* win, int n, float* lq, uint32_t round_t, cudaStream_t st) {
@@ -1415,8 +1415,14 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
         CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
     CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
              "gather patches");
-    CUDA_TRY(net_score(net, net->win, nwin, net->lq, nullptr, h->stream), "score");
     CUDA_TRY(net_sample(net, net->win2, nwin, net->lq2, rt, h->stream), "sample");
+    // log q of the current and of the proposed patch from the same function:
+    // in BF16 both come from the position-parallel scoring kernel (the
+    // sampler's own log q is replaced), in FP8 both from the sequential kernel
+    if (net->precision == ISING_NET_FP8)
+        CUDA_TRY(net_score(net, net->win, nwin, net->lq, nullptr, h->stream), "score");
+    else
+        CUDA_TRY(launch_net_score(net->ns, net->win, nwin, net->lq, nullptr, net->win2, net->lq2, h->stream), "score");
     CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
                              net->accepted, h->stream), "accept");
     if (host_accepted) {

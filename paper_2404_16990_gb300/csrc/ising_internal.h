@@ -145,6 +145,10 @@ int set_last_error(int code, const char* msg);
 cudaError_t configure_learned_kernels();
 cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
                                __nv_bfloat16* h, cudaStream_t stream);
+// Teacher-forced log q (and logits z if given) of n windows; with win_b also
+// the log q of the n windows at win_b into lq_b, in the same launch.
+cudaError_t launch_net_score(const NetState& ns, const int8_t* win, int n, float* lq, float* z, const int8_t* win_b,
+                             float* lq_b, cudaStream_t stream);
 cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
                               uint32_t round_t, cudaStream_t stream);
 cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, const float* z,
