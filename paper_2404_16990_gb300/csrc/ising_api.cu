@@ -1415,7 +1415,9 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
         CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
     CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
              "gather patches");
-    CUDA_TRY(net_sample(net, net->win2, nwin, net->lq2, rt, h->stream), "sample");
+    // BF16: the sampler's own log q is not needed (both patches are scored below)
+    CUDA_TRY(net_sample(net, net->win2, nwin, net->precision == ISING_NET_FP8 ? net->lq2 : nullptr, rt, h->stream),
+             "sample");
     // log q of the current and of the proposed patch from the same function:
     // in BF16 both come from the position-parallel scoring kernel (the
     // sampler's own log q is replaced), in FP8 both from the sequential kernel

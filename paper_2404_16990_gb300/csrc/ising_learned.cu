@@ -44,14 +44,12 @@ static_assert(kOffB4 + 1 == ISING_NET_PARAMS, "parameter layout");
 constexpr int kWarpsFwd = 4;
 constexpr int kWin = 8;                                       // windows per warp (rows 0..7 of the m16 tile)
 constexpr int kRowH = 24;                                     // bf16 per activation row: 16 + 8 padding
-// per-warp shared memory of the BF16 forward kernel: spins [8][100] int8, the
-// activation ring [3 layers][12 slots][8 windows][24] bf16 (rows padded so the
-// fragment loads of 8 rows x 4 lanes hit 32 distinct banks), and the sampling
-// draws [8][64] u32
+// per-warp shared memory of the sequential BF16 forward kernel: spins [8][100]
+// int8 and the activation ring [3 layers][12 slots][8 windows][24] bf16 (rows
+// padded so the fragment loads of 8 rows x 4 lanes hit 32 distinct banks)
 constexpr int kSpinBytes = kWin * kNPos;                      // 800
 constexpr int kRingBytes = 3 * kSlots * kWin * kRowH * 2;     // 13824
-constexpr int kDrawBytes = kWin * 64 * 4;                     // 2048
-constexpr int kWarpSmem = kSpinBytes + kRingBytes + kDrawBytes;   // 16672 (multiple of 16)
+constexpr int kWarpSmem = kSpinBytes + kRingBytes;            // 14624 (multiple of 16)
 
 // (dy, dx) of the "mask B" taps and of the layer-1 features
 __constant__ int8_t c_tapB[5][2] = {{-1, -1}, {-1, 0}, {-1, 1}, {0, -1}, {0, 0}};
@@ -95,25 +93,22 @@ struct NetPtrs {
 };
 
 // ---------------------------------------------------------------------------
-// Sequential forward over the 100 window positions for 8 windows per warp
-// (rows 0..7 of each m16 tile; rows 8..15 are zero).  MODE 0 scores given
-// windows (teacher forcing); MODE 1 samples the interior.  Writes lq[w] =
-// log q(window w) (fp32 sum), and optionally the logits z[w][p] and the
-// activations h[l][w][p][c] (training).
+// Sequential teacher-forced forward over the 100 window positions for 8
+// windows per warp (rows 0..7 of each m16 tile; rows 8..15 are zero), the
+// forward pass of training.  Writes lq[w] = log q(window w) (fp32 sum), and
+// optionally the logits z[w][p] and the activations h[l][w][p][c] that the
+// backward kernel reads.
 //
 // In the m16n8k16 layout the C fragment a thread holds for an output position
 // (row g, channels 2tq, 2tq+1, 8+2tq, 9+2tq) is exactly the A fragment the next
 // layer needs from that position, so the (0,0) and (0,-1) taps of layers 2-4
 // come from registers; only the three taps of the previous row go through a
 // shared-memory ring written once per position and read about ten positions
-// later.  The sampling draws are made before the position loop, and a sampled
-// spin reaches the other lanes of its window by a shuffle.  Layers 2-4
-// accumulate their taps in two independent chains summed at the end.
+// later.  Layers 2-4 accumulate their taps in independent chains summed at
+// the end.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int8_t* win, int n, float* lq,
-                                                                 float* z_out, __nv_bfloat16* h_out,
-                                                                 const LearnedKey* keys, uint32_t round_t) {
+__global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, const int8_t* win, int n, float* lq,
+                                                                 float* z_out, __nv_bfloat16* h_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
@@ -122,25 +117,12 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
     unsigned char* wbase = smem + warp * kWarpSmem;
     int8_t* sp = reinterpret_cast<int8_t*>(wbase);
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(wbase + kSpinBytes);
-    uint32_t* draws = reinterpret_cast<uint32_t*>(wbase + kSpinBytes + kRingBytes);   // [8][64]
     auto H = [&](int layer, int slot, int row) -> __nv_bfloat16* {
         return ring + ((layer * kSlots + slot) * kWin + row) * kRowH;
     };
     for (int i = lane; i < kWin * kNPos; i += 32) {
         const int row = i / kNPos;
         sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
-    }
-    if (MODE == 1) {   // the 64 draws of every window: 16 Philox blocks each
-        for (int b = lane; b < kWin * 16; b += 32) {
-            const int row = b >> 4, q = b & 15, w = w0 + row;
-            uint4 rv = make_uint4(0u, 0u, 0u, 0u);
-            if (w < n) {
-                const LearnedKey k = keys[w];
-                rv = philox(16u * k.j + (uint32_t)q, round_t, k.sim, 4u, k.key0, k.key1);
-            }
-            uint32_t* d = draws + row * 64 + 4 * q;
-            d[0] = rv.x; d[1] = rv.y; d[2] = rv.z; d[3] = rv.w;
-        }
     }
     // weights -> B fragments (registers)
     uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[5][2];
@@ -279,19 +261,8 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
             const float z = (((d4[0][0] + d4[1][0]) + (d4[2][0] + d4[3][0])) + d4[4][0]) + b4;   // lanes tq == 0
             float xs = 0.0f;
             if (interior(r, c)) {
-                const int w = w0 + g;
-                int8_t x = sp[g * kNPos + p];
-                if (tq == 0 && w < n) {
-                    if (MODE == 1) {
-                        const uint32_t u = draws[g * 64 + (r - 1) * kP + (c - 1)];
-                        const float sg = 1.0f / (1.0f + expf(-z));
-                        const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
-                        x = (u < thr) ? (int8_t)1 : (int8_t)-1;
-                        sp[g * kNPos + p] = x;
-                    }
-                    lq_acc += log_sigmoid((float)x * z);
-                }
-                if (MODE == 1) x = (int8_t)__shfl_sync(0xffffffffu, (int)x, lane & ~3);
+                const int8_t x = sp[g * kNPos + p];
+                if (tq == 0 && w0 + g < n) lq_acc += log_sigmoid((float)x * z);
                 xs = (float)x;
             }
             if (tq == 0 && w0 + g < n && z_out) z_out[(size_t)(w0 + g) * kNPos + p] = z;
@@ -302,13 +273,6 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, int
         }
     }
     if (tq == 0 && w0 + g < n) lq[w0 + g] = lq_acc;
-    if (MODE == 1) {
-        __syncwarp();
-        for (int i = lane; i < kWin * kNPos; i += 32) {
-            const int row = i / kNPos;
-            if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -563,6 +527,278 @@ __global__ void __launch_bounds__(kWarpsScore * 32, 4) ar_score_kernel(NetPtrs n
         for (int o = 16; o > 0; o >>= 1) lq_acc += __shfl_down_sync(0xffffffffu, lq_acc, o);
         if (lane == 0) (second ? lq_b : lq_a)[wi] = lq_acc;
         __syncwarp();                   // the buffers are rewritten by the next window
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Autoregressive sampling by wavefronts.  The logit of position (r, c)
+// depends on spins and activations at (r', c') with r' < r and c' <= c + (r - r')
+// (c' <= c in row r - 1) or r' = r, c' < c, so every position on the line
+// s = c + 2r can be sampled at once once the lines before it are done: 28
+// steps of at most five positions replace the 100 sequential positions, with
+// the same arithmetic at every position (the sampled spins equal the raster
+// order's).  One warp carries three windows; the rows of its m16 tile are
+// (window w, k-th position of the step), row 5w + k (row 15 idle).
+//
+// Per step: the four taps of layers 2 and 3 that come from the three previous
+// steps are gathered by ldmatrix from per-window rings (the last four steps'
+// layer-1 and layer-2 outputs) and multiplied first, into accumulators that
+// start at the bias; then layer 1 (A fragment from padded spin arrays of
+// interior and ring sites, as in the scoring kernel), and the (0, 0) taps of
+// layers 2 and 3 straight from registers (the C fragment of a layer is the A
+// fragment of the next); layer 4 is one n8 mma giving u[t] = H3 . W4[t] per
+// row, kept in a ring, and the logit is b4 + sum_t u[source_t][t].  Lanes
+// 0 .. 14 then sample their row's site from its draw.  Rows that are idle in
+// a step read the zero slot and write a trash slot.  Per-step row geometry
+// comes from two block-shared tables.
+// ---------------------------------------------------------------------------
+constexpr int kSteps = 3 * kS - 2;                     // s = c + 2r in [0, 27]
+constexpr int kPerStep = 5;
+constexpr int kWinT = 3;                               // windows per warp
+constexpr int kWarpsSmp = 4;
+constexpr int kRingSlots = 4 * kPerStep;               // rows of the last four steps
+constexpr int kZeroSlot = kRingSlots, kTrashSlot = kRingSlots + 1;
+constexpr int kLayerRows = kRingSlots + 2;             // 22 rows of one layer's ring
+constexpr int kSmpRing = 2 * kLayerRows * kRowBytes;   // layers 1 and 2: 2112 bytes
+constexpr int kSmpSpin = kSmpRing;                     // interior then ring spins, bf16 bits
+constexpr int kSmpU = kSmpSpin + 2 * 2 * kSpinRows;    // u ring: kLayerRows x 5 floats (+2)
+constexpr int kSmpDraws = kSmpU + 112 * 4;             // 64 draws
+constexpr int kSmpWinBytes = kSmpDraws + 64 * 4;       // 3360
+// window stride: 16-byte chunk index = 7 (mod 8), so that the tile rows 5w + k
+// of one step fall into distinct bank groups at the 48-byte row pitch
+constexpr int kSmpWinStride = (kSmpWinBytes / 16 + (15 - (kSmpWinBytes / 16) % 8) % 8) * 16;   // 3440
+static_assert(kSmpWinBytes % 16 == 0 && kSmpWinStride >= kSmpWinBytes && kSmpWinStride - kSmpWinBytes < 128 &&
+                  (kSmpWinStride / 16) % 8 == 7, "window stride");
+static_assert(kLayerRows * 5 <= 112, "u ring");
+// tables: per (step, tile row) 8 bytes {source slot of taps 0..4, own slot (or
+// trash), draw index (0xFF: nothing to sample), padded site row}; per (step,
+// g) 4 bytes {padded site rows of tile rows g and g + 8, their own slots}
+constexpr int kSmpTabR = kSteps * 16 * 8;
+constexpr int kSmpTabC = kSteps * 8 * 4;
+constexpr int kSmpSmem = kWarpsSmp * kWinT * kSmpWinStride + kSmpTabR + kSmpTabC;
+
+__device__ __forceinline__ int step_rmin(int s) { return s >= 9 ? (s - 8) / 2 : 0; }
+__device__ __forceinline__ int step_count(int s) { return min(kS - 1, s / 2) - step_rmin(s) + 1; }
+// d = a b + c with c = (c0, c1) in both row halves: the bias as the accumulator input
+__device__ __forceinline__ void mma16816_bias(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2],
+                                              float c0, float c1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%10,%11};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(c0), "f"(c1));
+}
+
+__global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_kernel(NetPtrs net, int8_t* win, int n, float* lq,
+                                                                  const LearnedKey* keys, uint32_t round_t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    uint2* tabR = reinterpret_cast<uint2*>(smem + kWarpsSmp * kWinT * kSmpWinStride);
+    uint32_t* tabC = reinterpret_cast<uint32_t*>(smem + kWarpsSmp * kWinT * kSmpWinStride + kSmpTabR);
+    for (int i = threadIdx.x; i < kSteps * 16; i += blockDim.x) {
+        const int st = i >> 4, row = i & 15, k = row % kPerStep;
+        uint32_t b[8] = {kZeroSlot, kZeroSlot, kZeroSlot, kZeroSlot, kZeroSlot, kTrashSlot, 0xFFu, kRow0};
+        if (row < kPerStep * kWinT && k < step_count(st)) {
+            const int r = step_rmin(st) + k, c = st - 2 * r;
+#pragma unroll 1
+            for (int t = 0; t < 5; ++t) {
+                const int y = r + c_tapB[t][0], x = c + c_tapB[t][1];
+                if (y >= 0 && x >= 0 && x < kS) b[t] = kPerStep * ((x + 2 * y) & 3) + (y - step_rmin(x + 2 * y));
+            }
+            b[5] = kPerStep * (st & 3) + k;
+            if (interior(r, c)) b[6] = (r - 1) * kP + (c - 1);
+            b[7] = (r + 1) * kPW + c + 1;
+        }
+        tabR[i] = make_uint2(b[0] | b[1] << 8 | b[2] << 16 | b[3] << 24, b[4] | b[5] << 8 | b[6] << 16 | b[7] << 24);
+    }
+    for (int i = threadIdx.x; i < kSteps * 8; i += blockDim.x) {
+        const int st = i >> 3, gg = i & 7;
+        uint32_t v = 0;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int row = gg + 8 * h, k = row % kPerStep;
+            uint32_t q = kRow0, own = kTrashSlot;
+            if (row < kPerStep * kWinT && k < step_count(st)) {
+                const int r = step_rmin(st) + k, c = st - 2 * r;
+                q = (r + 1) * kPW + c + 1;
+                own = kPerStep * (st & 3) + k;
+            }
+            v |= q << (8 * h) | own << (16 + 8 * h);
+        }
+        tabC[i] = v;
+    }
+    unsigned char* wb = smem + warp * kWinT * kSmpWinStride;
+    auto wbase = [&](int w) -> unsigned char* { return wb + w * kSmpWinStride; };
+    uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[2];
+    load_b(net.wb + kOffW1, kC, 0, kC, bw1[0]);
+    load_b(net.wb + kOffW1, kC, 8, kC, bw1[1]);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        load_b(net.wb + kOffW2 + t * 256, kC, 0, kC, bw2[t][0]);
+        load_b(net.wb + kOffW2 + t * 256, kC, 8, kC, bw2[t][1]);
+        load_b(net.wb + kOffW3 + t * 256, kC, 0, kC, bw3[t][0]);
+        load_b(net.wb + kOffW3 + t * 256, kC, 8, kC, bw3[t][1]);
+    }
+    {
+        auto at = [&](int k) -> float { return g < 5 ? __bfloat162float(net.wb[kOffW4 + g * kC + k]) : 0.0f; };
+        bw4[0] = pack_bf16(at(2 * tq), at(2 * tq + 1));
+        bw4[1] = pack_bf16(at(2 * tq + 8), at(2 * tq + 9));
+    }
+    float bias[3][2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int co = nt * 8 + 2 * tq + e;
+            bias[0][nt][e] = net.wf[kOffB1 + co];
+            bias[1][nt][e] = net.wf[kOffB2 + co];
+            bias[2][nt][e] = net.wf[kOffB3 + co];
+        }
+    const float b4 = net.wf[kOffB4];
+    // this lane's four layer-1 features (2tq, 2tq+1, 2tq+8, 2tq+9): offsets into
+    // the window's spin arrays (the ring copy kSpinRows further) and masks
+    int foff[4];
+    uint32_t fmask[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 2 * tq + (e & 1) + ((e >> 1) ? 8 : 0), kind = c_feat[k][2];
+        foff[e] = kind == 2 ? 0 : (kind == 1 ? kSpinRows : 0) + c_feat[k][0] * kPW + c_feat[k][1];
+        fmask[e] = kind == 2 ? 0u : 0xFFFFu;
+    }
+    // the window of this lane's ldmatrix row (lane & 15; row 15 idle -> window 2) and of its C rows g, g + 8
+    const int lr = lane & 15, lwc = min(lr / kPerStep, kWinT - 1);
+    const int cw0 = g / kPerStep, cw1c = min((g + 8) / kPerStep, kWinT - 1);
+    const uint32_t ring_l = (uint32_t)__cvta_generic_to_shared(wbase(lwc)) + (uint32_t)(lane >> 4) * 16u;
+    const uint16_t* spin0 = reinterpret_cast<const uint16_t*>(wbase(cw0) + kSmpSpin);
+    const uint16_t* spin1 = reinterpret_cast<const uint16_t*>(wbase(cw1c) + kSmpSpin);
+    float* u0 = reinterpret_cast<float*>(wbase(cw0) + kSmpU);
+    float* u1 = reinterpret_cast<float*>(wbase(cw1c) + kSmpU);
+    unsigned char* wl = wbase(lwc);
+    const float* ul = reinterpret_cast<const float*>(wl + kSmpU);
+    __syncthreads();
+
+    constexpr uint32_t kL2 = kLayerRows * kRowBytes;       // the layer-2 ring after the layer-1 ring
+    // persistent over groups of three windows
+    for (int w0 = (blockIdx.x * kWarpsSmp + warp) * kWinT; w0 < n; w0 += gridDim.x * kWarpsSmp * kWinT) {
+    // zero the rings (zero slots included), spins, u ring; the input window's ring sites; the draws
+    for (int i = lane; i < kWinT * kSmpWinStride / 4; i += 32) reinterpret_cast<uint32_t*>(wb)[i] = 0u;
+    __syncwarp();
+    for (int i = lane; i < kWinT * kNPos; i += 32) {
+        const int w = i / kNPos, p = i - w * kNPos;
+        if (w0 + w < n && !interior(p / kS, p % kS)) {
+            const int8_t x = win[(size_t)(w0 + w) * kNPos + p];
+            reinterpret_cast<uint16_t*>(wbase(w) + kSmpSpin)[kSpinRows + padded_row(p)] =
+                x > 0 ? 0x3F80u : (x < 0 ? 0xBF80u : 0u);
+        }
+    }
+    for (int bq = lane; bq < kWinT * 16; bq += 32) {
+        const int w = bq >> 4, q = bq & 15;
+        if (w0 + w < n) {
+            const LearnedKey k = keys[w0 + w];
+            const uint4 rv = philox(16u * k.j + (uint32_t)q, round_t, k.sim, 4u, k.key0, k.key1);
+            uint32_t* d = reinterpret_cast<uint32_t*>(wbase(w) + kSmpDraws) + 4 * q;
+            d[0] = rv.x; d[1] = rv.y; d[2] = rv.z; d[3] = rv.w;
+        }
+    }
+    __syncwarp();
+    float lq_acc = 0.0f;
+#pragma unroll 1
+    for (int s = 0; s < kSteps; ++s) {
+        const uint2 dr = tabR[s * 16 + lr];
+        const uint32_t dc = tabC[s * 8 + g];
+        const uint32_t sl0 = dr.x & 0xFF, sl1 = (dr.x >> 8) & 0xFF, sl2 = (dr.x >> 16) & 0xFF, sl3 = dr.x >> 24;
+        const uint32_t sl4 = dr.y & 0xFF, own = (dr.y >> 8) & 0xFF;
+        // ---- the ring taps of layers 2 and 3, into bias-initialised accumulators ----
+        float d2[2][4], d3[2][4];
+        {
+            uint32_t at[4][4];
+            ldmatrix_x4(at[0], ring_l + sl0 * kRowBytes);
+            ldmatrix_x4(at[1], ring_l + sl1 * kRowBytes);
+            ldmatrix_x4(at[2], ring_l + sl2 * kRowBytes);
+            ldmatrix_x4(at[3], ring_l + sl3 * kRowBytes);
+            mma16816_bias(d2[0], at[0], bw2[0][0], bias[1][0][0], bias[1][0][1]);
+            mma16816_bias(d2[1], at[0], bw2[0][1], bias[1][1][0], bias[1][1][1]);
+#pragma unroll
+            for (int t = 1; t < 4; ++t) { mma16816(d2[0], at[t], bw2[t][0]); mma16816(d2[1], at[t], bw2[t][1]); }
+            ldmatrix_x4(at[0], ring_l + kL2 + sl0 * kRowBytes);
+            ldmatrix_x4(at[1], ring_l + kL2 + sl1 * kRowBytes);
+            ldmatrix_x4(at[2], ring_l + kL2 + sl2 * kRowBytes);
+            ldmatrix_x4(at[3], ring_l + kL2 + sl3 * kRowBytes);
+            mma16816_bias(d3[0], at[0], bw3[0][0], bias[2][0][0], bias[2][0][1]);
+            mma16816_bias(d3[1], at[0], bw3[0][1], bias[2][1][0], bias[2][1][1]);
+#pragma unroll
+            for (int t = 1; t < 4; ++t) { mma16816(d3[0], at[t], bw3[t][0]); mma16816(d3[1], at[t], bw3[t][1]); }
+        }
+        // ---- layer 1 ----
+        const int q0 = dc & 0xFF, q1 = (dc >> 8) & 0xFF;
+        uint32_t h[4];
+        {
+            uint32_t f0[4], f1[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                f0[e] = spin0[q0 + foff[e]] & fmask[e];
+                f1[e] = spin1[q1 + foff[e]] & fmask[e];
+            }
+            const uint32_t a[4] = {f0[0] | (f0[1] << 16), f1[0] | (f1[1] << 16), f0[2] | (f0[3] << 16),
+                                   f1[2] | (f1[3] << 16)};
+            float d[2][4];
+            mma16816_bias(d[0], a, bw1[0], bias[0][0][0], bias[0][0][1]);
+            mma16816_bias(d[1], a, bw1[1], bias[0][1][0], bias[0][1][1]);
+            h[0] = pack_bf16_relu(d[0][0], d[0][1]); h[1] = pack_bf16_relu(d[0][2], d[0][3]);
+            h[2] = pack_bf16_relu(d[1][0], d[1][1]); h[3] = pack_bf16_relu(d[1][2], d[1][3]);
+            stmatrix_x4(ring_l + own * kRowBytes, h[0], h[1], h[2], h[3]);
+        }
+        // ---- layers 2 and 3: the (0, 0) taps ----
+        mma16816(d2[0], h, bw2[4][0]);
+        mma16816(d2[1], h, bw2[4][1]);
+        h[0] = pack_bf16_relu(d2[0][0], d2[0][1]); h[1] = pack_bf16_relu(d2[0][2], d2[0][3]);
+        h[2] = pack_bf16_relu(d2[1][0], d2[1][1]); h[3] = pack_bf16_relu(d2[1][2], d2[1][3]);
+        stmatrix_x4(ring_l + kL2 + own * kRowBytes, h[0], h[1], h[2], h[3]);
+        mma16816(d3[0], h, bw3[4][0]);
+        mma16816(d3[1], h, bw3[4][1]);
+        h[0] = pack_bf16_relu(d3[0][0], d3[0][1]); h[1] = pack_bf16_relu(d3[0][2], d3[0][3]);
+        h[2] = pack_bf16_relu(d3[1][0], d3[1][1]); h[3] = pack_bf16_relu(d3[1][2], d3[1][3]);
+        // ---- layer 4: u[t] of rows g, g + 8 (columns 2tq, 2tq + 1) into the u ring ----
+        {
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+            mma16816(d4, h, bw4);
+            const int c0 = 2 * tq, o0 = (int)((dc >> 16) & 0xFF) * 5 + c0, o1 = (int)(dc >> 24) * 5 + c0;
+            if (c0 < 5) { u0[o0] = d4[0]; u1[o1] = d4[2]; }
+            if (c0 + 1 < 5) { u0[o0 + 1] = d4[1]; u1[o1 + 1] = d4[3]; }
+        }
+        __syncwarp();
+        // ---- sample: lane lr < 15 takes its row's site when it has one ----
+        const uint32_t di = (dr.y >> 16) & 0xFF;
+        if (lane < 16 && di != 0xFFu) {
+            const float z = b4 + ul[sl0 * 5 + 0] + ul[sl1 * 5 + 1] + ul[sl2 * 5 + 2] + ul[sl3 * 5 + 3] + ul[sl4 * 5 + 4];
+            const uint32_t draw = reinterpret_cast<const uint32_t*>(wl + kSmpDraws)[di];
+            const float sg = __frcp_rn(1.0f + expf(-z));        // = 1 / (1 + e^-z), correctly rounded
+            const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
+            const float x = draw < thr ? 1.0f : -1.0f;
+            reinterpret_cast<uint16_t*>(wl + kSmpSpin)[dr.y >> 24] = x > 0.f ? 0x3F80u : 0xBF80u;
+            if (lq) lq_acc += log_sigmoid(x * z);
+        }
+        __syncwarp();
+    }
+    // log q per window: lanes 5w .. 5w + 4
+    float* lqs = reinterpret_cast<float*>(wb + kSmpU);     // window 0's u ring is free now
+    if (lane < 16) lqs[lane] = lq_acc;
+    __syncwarp();
+    if (lane < kWinT && w0 + lane < n && lq) {
+        float t = 0.0f;
+        for (int k = 0; k < kPerStep; ++k) t += lqs[kPerStep * lane + k];
+        lq[w0 + lane] = t;
+    }
+    // the sampled interiors back into the windows
+    for (int i = lane; i < kWinT * kNPos; i += 32) {
+        const int w = i / kNPos, p = i - w * kNPos;
+        if (w0 + w < n && interior(p / kS, p % kS)) {
+            const uint16_t v = reinterpret_cast<const uint16_t*>(wbase(w) + kSmpSpin)[padded_row(p)];
+            win[(size_t)(w0 + w) * kNPos + p] = v == 0x3F80u ? (int8_t)1 : (int8_t)-1;
+        }
+    }
+    __syncwarp();                       // the window buffers are cleared for the next group
     }
 }
 
@@ -1045,12 +1281,12 @@ __global__ void mh_apply_kernel(DevState st, const LearnedLat* ll, int n_lat, in
 static int fwd_blocks(int n) { return (n + kWin * kWarpsFwd - 1) / (kWin * kWarpsFwd); }
 
 cudaError_t configure_learned_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(ar_net_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(ar_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kWarpsFwd * kWarpSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ar_net_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpsFwd * kWarpSmem);
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ar_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ar_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmpSmem);
     const int bwd = (((kNParams + 3) / 4) * 4 + kWarpsBwd * 2 * kNPos * kC) * (int)sizeof(float);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(net_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd);
@@ -1071,8 +1307,7 @@ cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, flo
                                cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     NetPtrs np{ns.wb, ns.w};
-    ar_net_kernel<0><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(
-        np, const_cast<int8_t*>(win), n, lq, z, h, nullptr, 0u);
+    ar_net_kernel<<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(np, win, n, lq, z, h);
     return cudaGetLastError();
 }
 
@@ -1101,8 +1336,8 @@ cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq,
                               uint32_t round_t, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     NetPtrs np{ns.wb, ns.w};
-    ar_net_kernel<1><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(np, win, n, lq, nullptr,
-                                                                                     nullptr, keys, round_t);
+    const int blocks = std::min((n + kWarpsSmp * kWinT - 1) / (kWarpsSmp * kWinT), device_sm_count() * 4);
+    ar_sample_kernel<<<blocks, kWarpsSmp * 32, kSmpSmem, stream>>>(np, win, n, lq, keys, round_t);
     return cudaGetLastError();
 }
 
