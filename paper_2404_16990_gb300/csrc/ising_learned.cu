@@ -1200,77 +1200,142 @@ __global__ void train_windows_kernel(const uint32_t* pool, int n_snap, uint32_t 
 }
 
 // Patch windows of every lattice of a handle for one round, and their keys.
-__global__ void gather_patches_kernel(DevState st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
-                                      uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nwin * kNPos; i += gridDim.x * blockDim.x) {
-        const int w = i / kNPos, p = i % kNPos;
-        int lo = 0, hi = n_lat - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int)ll[mid].patch_begin <= w) lo = mid; else hi = mid - 1;
-        }
-        const LearnedLat d = ll[lo];
-        const uint32_t L = d.L, per_row = L / 16, j = (uint32_t)w - d.patch_begin;
-        const uint32_t a = j % per_row, b = j / per_row;
-        const uint32_t x0 = (16u * a + ox) % L, y0 = (16u * b + oy) % L;
-        const uint32_t y = (y0 + L - 1 + p / kS) % L, x = (x0 + L - 1 + p % kS) % L;
-        const int8_t s = packed_spin(st.spins + d.word_off, L, x, y);
-        win[i] = s;
-        win2[i] = s;
-        if (p == 0) keys[w] = LearnedKey{d.key0, d.key1, d.sim, j};
+// The lattice of patch w (the same w in every lane): the last entry with
+// patch_begin <= w (entry 0 begins at 0), by a 32-way search -- each round
+// the lanes probe 32 evenly spaced entries of the remaining range and a ballot
+// keeps the last one at or below w (one round up to 32 lattices, two up to 1024).
+__device__ __forceinline__ int patch_lattice_warp(const LearnedLat* ll, int n_lat, int w, int lane) {
+    int lo = 0, span = n_lat;
+    while (span > 1) {
+        const int step = (span + 31) / 32, idx = lo + lane * step;
+        const bool le = lane * step < span && (int)ll[idx].patch_begin <= w;
+        const int k = 31 - __clz(__ballot_sync(0xffffffffu, le));
+        lo += k * step;
+        span = min(step, span - k * step);
     }
+    return lo;
 }
 
-// Energy of the bonds touching the interior of a window.
-__device__ int local_energy(const int8_t* w) {
-    int e = 0;
-    for (int r = 1; r <= kP; ++r)
-        for (int c = 0; c < kS - 1; ++c) e -= w[r * kS + c] * w[r * kS + c + 1];
-    for (int c = 1; c <= kP; ++c)
-        for (int r = 0; r < kS - 1; ++r) e -= w[r * kS + c] * w[(r + 1) * kS + c];
-    return e;
+// One warp per patch: its window (the 8 x 8 patch with the ring around it)
+// into win and win2, and its key.
+__global__ void gather_patches_kernel(DevState st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
+                                      uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys) {
+    const int lane = threadIdx.x & 31;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += (gridDim.x * blockDim.x) >> 5) {
+        const LearnedLat d = ll[patch_lattice_warp(ll, n_lat, w, lane)];
+        const uint32_t L = d.L, per_row = L / 16, j = (uint32_t)w - d.patch_begin;
+        const uint32_t xs = (16u * (j % per_row) + ox + L - 1) % L, ys = (16u * (j / per_row) + oy + L - 1) % L;
+        const uint32_t* base = st.spins + d.word_off;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = lane + 32 * i;
+            if (p < kNPos) {
+                uint32_t x = xs + (uint32_t)(p % kS), y = ys + (uint32_t)(p / kS);
+                if (x >= L) x -= L;
+                if (y >= L) y -= L;
+                const int8_t sv = packed_spin(base, L, x, y);
+                win[(size_t)w * kNPos + p] = sv;
+                win2[(size_t)w * kNPos + p] = sv;
+            }
+        }
+        if (lane == 0) keys[w] = LearnedKey{d.key0, d.key1, d.sim, j};
+    }
 }
 
 // Metropolis-Hastings acceptance (FP64) and write-back of accepted patches.
-__global__ void mh_apply_kernel(DevState st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox, uint32_t oy,
-                                const int8_t* win_old, const int8_t* win_new, const float* lq_old,
-                                const float* lq_new, uint32_t round_t, unsigned long long* accepted) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwin) return;
-    int lo = 0, hi = n_lat - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((int)ll[mid].patch_begin <= w) lo = mid; else hi = mid - 1;
-    }
-    const LearnedLat d = ll[lo];
-    const int8_t* xo = win_old + (size_t)w * kNPos;
-    const int8_t* xn = win_new + (size_t)w * kNPos;
-    const int dE = local_energy(xn) - local_energy(xo);
-    const double log_alpha = -(double)dE * d.beta + (double)lq_old[w] - (double)lq_new[w];
-    const uint32_t j = (uint32_t)w - d.patch_begin;
-    const uint4 r = philox(j, round_t, d.sim, 5u, d.key0, d.key1);
-    const double u = ((double)((r.x >> 5) * 67108864ull + (r.y >> 6)) + 0.5) / 9007199254740992.0;
-    if (!(log(u) < log_alpha)) return;
-    const uint32_t L = d.L, wn = L >> 6, per_row = L / 16, a = j % per_row, b = j / per_row;
-    const uint32_t x0 = (16u * a + ox) % L, y0 = (16u * b + oy) % L;
-    int dM = 0;
-    for (int rr = 0; rr < kP; ++rr) {
-        const uint32_t y = (y0 + rr) % L;
-        uint32_t mask[2] = {0u, 0u};
-        uint32_t widx[2] = {0u, 0u};
-        for (int cc = 0; cc < kP; ++cc) {
-            const int8_t so = xo[(rr + 1) * kS + cc + 1], sn = xn[(rr + 1) * kS + cc + 1];
-            dM += sn - so;
-            const uint32_t x = (x0 + cc) % L, c = (x + y) & 1u, jj = x >> 1;
-            widx[c] = ((uint32_t)c * L + y) * wn + (jj >> 5);
-            if (so != sn) mask[c] |= 1u << (jj & 31);
+// A warp takes 32 consecutive patches: their old and new windows are staged
+// in shared memory (3200 contiguous bytes each, 16-byte loads); lane k then
+// computes patch k's change of the energy of the bonds touching the interior
+// and of the interior magnetization (the 100-byte window stride is 25 words,
+// so the lanes hit 32 distinct banks) and takes its FP64 decision (all lanes
+// at once: the FP64 pipe is narrow); the accepted patches are written back
+// one after another by the warp.
+constexpr int kMhWarps = 4;
+__global__ void __launch_bounds__(kMhWarps * 32) mh_apply_kernel(DevState st, const LearnedLat* ll, int n_lat,
+                                                                int nwin, uint32_t ox, uint32_t oy,
+                                                                const int8_t* win_old, const int8_t* win_new,
+                                                                const float* lq_old, const float* lq_new,
+                                                                uint32_t round_t, unsigned long long* accepted) {
+    __shared__ __align__(16) int8_t sw[kMhWarps][2][32 * kNPos];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wbase = (blockIdx.x * kMhWarps + warp) * 32;
+    if (wbase >= nwin) return;
+    const int nw = min(32, nwin - wbase);
+    int8_t* xo = sw[warp][0];
+    int8_t* xn = sw[warp][1];
+    const int8_t* go = win_old + (size_t)wbase * kNPos;
+    const int8_t* gn = win_new + (size_t)wbase * kNPos;
+    if (nw == 32) {                     // wbase * 100 is a multiple of 3200: 16-byte aligned
+        for (int i = lane; i < 32 * kNPos / 16; i += 32) {
+            reinterpret_cast<uint4*>(xo)[i] = reinterpret_cast<const uint4*>(go)[i];
+            reinterpret_cast<uint4*>(xn)[i] = reinterpret_cast<const uint4*>(gn)[i];
         }
-        for (int c = 0; c < 2; ++c)
-            if (mask[c]) atomicXor(&st.spins[d.word_off + widx[c]], mask[c]);
+    } else {
+        for (int i = lane; i < nw * kNPos; i += 32) { xo[i] = go[i]; xn[i] = gn[i]; }
     }
-    atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat]), (unsigned long long)(long long)dE);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat + 1]), (unsigned long long)(long long)dM);
-    atomicAdd(&accepted[d.lat], 1ull);
+    __syncwarp();
+    // the lattice of each lane's patch: from the first patch's, forward (32
+    // consecutive patches span few lattices: a lattice has at least 16)
+    int lat = patch_lattice_warp(ll, n_lat, wbase, lane);
+    if (lane < nw)
+        while (lat + 1 < n_lat && (int)ll[lat + 1].patch_begin <= wbase + lane) ++lat;
+    int e = 0, m = 0;
+    bool accept = false;
+    if (lane < nw) {
+        const int8_t* o = xo + lane * kNPos;
+        const int8_t* q = xn + lane * kNPos;
+        // bonds (r, c)-(r, c + 1), r in 1..8, c in 0..8, and (r, c)-(r + 1, c), c in 1..8, r in 0..8
+        for (int r = 1; r <= kP; ++r)
+            for (int c = 0; c < kS - 1; ++c) {
+                const int p = r * kS + c;
+                e -= q[p] * q[p + 1] - o[p] * o[p + 1];
+                if (c >= 1) m += q[p] - o[p];
+            }
+        for (int c = 1; c <= kP; ++c)
+            for (int r = 0; r < kS - 1; ++r) {
+                const int p = r * kS + c;
+                e -= q[p] * q[p + kS] - o[p] * o[p + kS];
+            }
+        const int w = wbase + lane;
+        const LearnedLat d = ll[lat];
+        const uint32_t j = (uint32_t)w - d.patch_begin;
+        const double log_alpha = -(double)e * d.beta + (double)lq_old[w] - (double)lq_new[w];
+        const uint4 r = philox(j, round_t, d.sim, 5u, d.key0, d.key1);
+        const double u = ((double)((r.x >> 5) * 67108864ull + (r.y >> 6)) + 0.5) / 9007199254740992.0;
+        accept = log(u) < log_alpha;
+    }
+    for (uint32_t bal = __ballot_sync(0xffffffffu, accept); bal; bal &= bal - 1) {
+        const int k = __ffs(bal) - 1, wk = wbase + k;
+        const int ek = __shfl_sync(0xffffffffu, e, k), mk = __shfl_sync(0xffffffffu, m, k);
+        const LearnedLat d = ll[__shfl_sync(0xffffffffu, lat, k)];
+        const uint32_t j = (uint32_t)wk - d.patch_begin;
+        const int8_t* o = xo + k * kNPos;
+        const int8_t* q = xn + k * kNPos;
+        // lane 2 rr + c: the flipped sites of interior row rr in colour c, one xor
+        // (x0 is a multiple of 8 -- patch origins 16a + {0, 8} -- and L of 64, so
+        // the four sites of one colour in a row share one 32-bit word)
+        const uint32_t L = d.L, wn = L >> 6, per_row = L / 16;
+        const uint32_t x0 = (16u * (j % per_row) + ox) % L, y0 = (16u * (j / per_row) + oy) % L;
+        if (lane < 2 * kP) {
+            const int rr = lane >> 1;
+            const uint32_t c = (uint32_t)(lane & 1), y = (y0 + rr) % L;
+            uint32_t mask = 0u, widx = 0u;
+            for (int cc = 0; cc < kP; ++cc) {
+                const uint32_t x = (x0 + cc) % L;
+                if (((x + y) & 1u) != c) continue;
+                const uint32_t jj = x >> 1;
+                widx = (c * L + y) * wn + (jj >> 5);
+                if (o[(rr + 1) * kS + cc + 1] != q[(rr + 1) * kS + cc + 1]) mask |= 1u << (jj & 31);
+            }
+            if (mask) atomicXor(&st.spins[d.word_off + widx], mask);
+        }
+        if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat]), (unsigned long long)(long long)ek);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&st.obs[2 * d.lat + 1]),
+                      (unsigned long long)(long long)mk);
+            atomicAdd(&accepted[d.lat], 1ull);
+        }
+    }
 }
 
 }  // namespace
@@ -1374,7 +1439,7 @@ cudaError_t launch_train_windows(const uint32_t* pool, int n_snap, uint32_t L, i
 cudaError_t launch_gather_patches(const DevState& st, const LearnedLat* ll, int n_lat, int nwin, uint32_t ox,
                                   uint32_t oy, int8_t* win, int8_t* win2, LearnedKey* keys, cudaStream_t stream) {
     if (nwin <= 0) return cudaSuccess;
-    const int blocks = std::min((nwin * kNPos + 255) / 256, device_sm_count() * 8);
+    const int blocks = std::min((nwin + 7) / 8, device_sm_count() * 8);
     gather_patches_kernel<<<blocks, 256, 0, stream>>>(st, ll, n_lat, nwin, ox, oy, win, win2, keys);
     return cudaGetLastError();
 }
@@ -1383,8 +1448,8 @@ cudaError_t launch_mh_apply(const DevState& st, const LearnedLat* ll, int n_lat,
                             const int8_t* win_old, const int8_t* win_new, const float* lq_old, const float* lq_new,
                             uint32_t round_t, unsigned long long* accepted, cudaStream_t stream) {
     if (nwin <= 0) return cudaSuccess;
-    mh_apply_kernel<<<(nwin + 127) / 128, 128, 0, stream>>>(st, ll, n_lat, nwin, ox, oy, win_old, win_new, lq_old,
-                                                           lq_new, round_t, accepted);
+    mh_apply_kernel<<<(nwin + 32 * kMhWarps - 1) / (32 * kMhWarps), kMhWarps * 32, 0, stream>>>(
+        st, ll, n_lat, nwin, ox, oy, win_old, win_new, lq_old, lq_new, round_t, accepted);
     return cudaGetLastError();
 }
 
