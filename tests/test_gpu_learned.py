@@ -89,6 +89,33 @@ def test_sample_matches_oracle_except_near_ties():
     assert mism <= 2
 
 
+def test_sample_large_batch_matches_oracle_on_a_subset():
+    """8,000 windows: more window triples than the persistent sampler has
+    warps (4 blocks of 4 warps per SM), so some warps take a second triple;
+    200 windows, half of them from the tail, checked against the oracle."""
+    B = 8000
+    net = ising.IsingNet(max_windows=B)
+    flat = ol.init_params(21, gain=1.5)
+    net.set_params(flat)
+    win = rand_windows(B, 4)
+    seed, s, rnd = 0x5EED0042, 3, 5
+    keys = np.array([[seed & 0xFFFFFFFF, seed >> 32, s, j] for j in range(B)], np.uint32)
+    gw, glq = net.sample(win, keys, rnd)
+    pick = sorted(np.random.default_rng(8).choice(7200, 100, replace=False).tolist()) + list(range(B - 100, B))
+    R = np.stack([ol.sampling_draws(seed, s, j, rnd) for j in pick])
+    ow, olq, thr = ol.sample(win[pick], flat, R)
+    mism = 0
+    for i, j in enumerate(pick):
+        assert np.array_equal(gw[j].reshape(10, 10)[0], win[j][0])
+        k = _first_diff(gw[j].reshape(10, 10), ow[i])
+        if k < 0:
+            assert abs(glq[j] - olq[i]) < 5e-2
+            continue
+        mism += 1
+        assert abs(R[i, k] - thr[i, k]) < 1e-2 * 2**32, (j, k, R[i, k], thr[i, k])
+    assert mism <= 6
+
+
 def _round_compare(L, T, seed, rnd, flat, prec="bf16"):
     sim = ising.IsingSim(L, [T], seed)
     s0 = oracle.init(L, seed, 0)
