@@ -66,10 +66,12 @@ __device__ __forceinline__ int lattice_of_item(const Lat3* lat, int n, uint64_t 
     return lo;
 }
 
+// 2 acc + [r >= t] by the carry of r - t, as in the 2D sweep (madc for the
+// shift-in: 0.6 % faster at 1024^3, 3-4 % at 256^3 and 512^3).
 __device__ __forceinline__ uint32_t shift_in_not_below3(uint32_t acc, uint32_t r, uint32_t t) {
     uint32_t diff, out;
     asm("sub.cc.u32 %0, %2, %3;\n\t"
-        "addc.u32 %1, %4, %4;"
+        "madc.lo.u32 %1, %4, 2, 0;"
         : "=r"(diff), "=r"(out)
         : "r"(r), "r"(t), "r"(acc));
     (void)diff;
