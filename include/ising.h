@@ -209,7 +209,11 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
  * half-sweep over the lattices in device memory.  Tuning knobs (0 = default):
  * words_per_thread in {1, 2, 4} = 32-bit words per streaming thread and row;
  * rows_per_item = rows per streaming thread (lowered per lattice so that one tile
- * of a block never spans more rows than the lattice has); sweeps_per_unit = sweeps a
+ * of a block never spans more rows than the lattice has).  By default the
+ * streaming tiling is 4 words and 4 rows per thread, reduced (words first,
+ * then rows if rows_per_item is also 0) while the streamed lattices would
+ * give fewer blocks than one full wave on the device; ising_get_plan reports
+ * the tiling in use.  sweeps_per_unit = sweeps a
  * resident work unit runs before its group is stored; threads = block size
  * (a multiple of 32, at most 512 resident / 256 streaming).  No choice
  * changes any result bit. */

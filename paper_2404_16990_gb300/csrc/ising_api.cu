@@ -100,7 +100,7 @@ bool compute_layout(int n, const int* Ls, int64_t trace_cap, Layout* out) {
 struct Plan {
     int mode = ISING_PLAN_AUTO;
     int words_per_thread = 0;   // stream: V (0 = default)
-    int rows_per_item = 4;      // stream: R
+    int rows_per_item = 0;      // stream: R (0 = default)
     int stream_threads = 256;
     int sweeps_per_unit = 0;    // resident: k (0 = default)
     int resident_threads = 0;   // 0 = from group size
@@ -135,7 +135,8 @@ struct ising_handle {
     int res_grid = 0;
     int n_slats = 0;
     uint64_t total_tiles = 0;
-    int V = 1;
+    int V = 1;                  // streaming tiling in use: words per thread and row,
+    int R = 4;                  // and rows per thread
     int stream_grid = 0;
     int sms = 0;
     int64_t launches = 0;
@@ -253,15 +254,48 @@ int build_tables(ising_handle* h) {
 
     // streamed lattices: tiles of (tw word groups) x (th row groups of R rows)
     std::vector<StreamLat> slats;
-    // default: 4 words (128 sites) per thread and row, halved while a
-    // streamed lattice's row does not divide (the fastest tiling measured on
-    // large lattices)
-    int V = h->plan.words_per_thread > 0 ? h->plan.words_per_thread : 4;
-    for (int i : streamed)
-        while (V > 1 && (h->L[i] / 64) % V != 0) V /= 2;
-    h->V = V;
-    const int R = std::max(1, h->plan.rows_per_item);
     const int B = h->plan.stream_threads;
+    auto divides = [&](int v) {
+        for (int i : streamed)
+            if ((h->L[i] / 64) % v != 0) return false;
+        return true;
+    };
+    auto count_tiles = [&](int v, int r) {
+        uint64_t n = 0;
+        for (int i : streamed) {
+            const uint32_t groups = (uint32_t)(h->L[i] / 64) / (uint32_t)v;
+            const uint32_t tw = std::min<uint32_t>(groups, (uint32_t)B), th = (uint32_t)B / tw;
+            const uint32_t rl = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)r, (uint32_t)h->L[i] / th));
+            n += (uint64_t)((groups + tw - 1) / tw) * (((uint32_t)h->L[i] + th * rl - 1) / (th * rl));
+        }
+        return n;
+    };
+    int V = h->plan.words_per_thread, R = h->plan.rows_per_item > 0 ? h->plan.rows_per_item : 4;
+    if (V > 0) {
+        while (V > 1 && !divides(V)) V /= 2;
+    } else if (streamed.empty()) {
+        V = 4;
+    } else {
+        // default tiling by the number of blocks it gives (256 threads), from
+        // measurements of single lattices (flip/ns): 4 words x 4 rows per thread
+        // only for large streamed workloads (six 16384^2: 1,461), 2 x 2 from
+        // 1.5 blocks per SM (8192^2: 1,221 against 1,160 for 4 x 4; 4096^2:
+        // 838 against 512), 1 x 2 from half a block per SM (2048^2: 479
+        // against 125), else 1 x 1.  Rows stay as given if rows_per_item is set.
+        const bool rows_free = h->plan.rows_per_item == 0;
+        const uint64_t sms = (uint64_t)h->sms;
+        const struct { int v, r; uint64_t min_tiles; } cand[4] = {
+            {4, rows_free ? 4 : R, 4 * sms}, {2, rows_free ? 2 : R, 3 * sms / 2},
+            {1, rows_free ? 2 : R, sms / 2}, {1, rows_free ? 1 : R, 0}};
+        for (const auto& c : cand) {
+            if (!divides(c.v)) continue;
+            V = c.v;
+            R = c.r;
+            if (count_tiles(V, R) >= c.min_tiles) break;
+        }
+    }
+    h->V = V;
+    h->R = R;
     uint64_t tiles = 0;
     for (int i : streamed) {
         StreamLat s{};
@@ -761,7 +795,7 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
     p.mode = plan;
     p.words_per_thread = words_per_thread;
     p.sweeps_per_unit = sweeps_per_unit;
-    p.rows_per_item = rows_per_item ? rows_per_item : 4;
+    p.rows_per_item = rows_per_item;
     if (plan == ISING_PLAN_STREAM || plan == ISING_PLAN_PERSIST) {
         if (threads != 0 && threads > 256) return fail(ISING_EINVAL, "streaming kernel allows at most 256 threads");
         p.stream_threads = threads ? threads : 256;
@@ -916,7 +950,7 @@ int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_it
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (plan) *plan = h->plan.mode;
     if (words_per_thread) *words_per_thread = h->V;
-    if (rows_per_item) *rows_per_item = h->plan.rows_per_item;
+    if (rows_per_item) *rows_per_item = h->R;
     if (sweeps_per_unit) *sweeps_per_unit = h->plan.sweeps_per_unit;
     if (threads)
         *threads = (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST) ? h->plan.stream_threads

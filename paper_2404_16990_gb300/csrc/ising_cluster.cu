@@ -299,23 +299,63 @@ __global__ void __launch_bounds__(256) sw_merge_kernel(DevState st, SwState sw) 
 // Every tile-local root (bit mask left in the coin array by sw_local_kernel)
 // is resolved to its final root f and takes f's coin (the top bit of lane
 // f & 3 of block f >> 2), which replaces the mask bit; the flip then needs
-// only the coin bit of each site's tile-local root.  One thread per 32
-// consecutive sites (one coin word).
+// only the coin bit of each site's tile-local root.  One warp per tile (a
+// tile is 32 coin words): the tile's roots are dealt out evenly over the
+// lanes -- root j of the tile (in word order) goes to lane j mod 32, which
+// finds its word by a search over the warp's prefix counts and its bit by a
+// popcount search -- and the coins are gathered back per word in shared
+// memory.
 // ---------------------------------------------------------------------------
+static_assert(kWordsPerTile == 32, "one warp per tile in sw_resolve_kernel");
+// Position of the k-th (from 0) set bit of m, which has more than k set bits:
+// halve the window five times, skipping the low half when it holds <= k bits.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t k) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int width = 16; width > 0; width >>= 1) {
+        const uint32_t c = __popc(m & ((1u << width) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= width;
+            pos += (uint32_t)width;
+        }
+    }
+    return pos;
+}
 __global__ void __launch_bounds__(256) sw_resolve_kernel(DevState st, SwState sw) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (uint64_t)sw.total_tiles * kWordsPerTile) return;
-    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)(g / kWordsPerTile))];
-    const uint32_t w = (uint32_t)(g - (uint64_t)d.tile_begin * kWordsPerTile);   // word within the lattice
+    __shared__ uint32_t s_coin[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (tile >= sw.total_tiles) return;                 // whole warps
+    const SwLat d = sw.lat[lattice_of_tile(sw.lat, sw.n, (uint32_t)tile)];
+    const uint32_t w = (uint32_t)((tile - d.tile_begin) * kWordsPerTile) + (uint32_t)lane;   // word in the lattice
     uint32_t* lab = sw.label + d.site_off;
     uint32_t* coin_word = sw.coins + d.site_off / 32 + w;
     const uint32_t t = (uint32_t)st.ctl->t;
-    uint32_t m = *coin_word, coin = 0;
+    const uint32_t m = *coin_word;
+    uint32_t incl = __popc(m);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - __popc(m), total = __shfl_sync(0xffffffffu, incl, 31);
+    s_coin[warp][lane] = 0u;
+    __syncwarp();
     bool failed = false;
-    while (m) {
-        const uint32_t i = (uint32_t)__ffs(m) - 1u;
-        m &= m - 1u;
-        const uint32_t r = 32u * w + i;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        // owner lane: the last lane whose exclusive count is <= j
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, excl, o + step);
+            if (e <= j) o += step;
+        }
+        const uint32_t mo = __shfl_sync(0xffffffffu, m, o), eo = __shfl_sync(0xffffffffu, excl, o);
+        if (j >= total) continue;
+        const uint32_t i = nth_set_bit(mo, j - eo);
+        const uint32_t r = 32u * (w - (uint32_t)lane + (uint32_t)o) + i;
         const uint32_t f = find_global(lab, r);
         if (f == ~0u) {
             failed = true;
@@ -323,12 +363,13 @@ __global__ void __launch_bounds__(256) sw_resolve_kernel(DevState st, SwState sw
         }
         if (f != r) lab[r] = f;
         const uint4 v = philox(f >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
-        const uint32_t lane = f & 3u;
-        const uint32_t word = lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
-        coin |= (word >> 31) << i;
+        const uint32_t ln = f & 3u;
+        const uint32_t word = ln == 0 ? v.x : ln == 1 ? v.y : ln == 2 ? v.z : v.w;
+        if (word >> 31) atomicOr(&s_coin[warp][o], 1u << i);
     }
     if (failed) atomicExch(&st.ctl->error, kErrUnionBound);
-    *coin_word = coin;
+    __syncwarp();
+    *coin_word = s_coin[warp][lane];
 }
 
 // Every site points at its final root (only for ising_sw_labels): the link
