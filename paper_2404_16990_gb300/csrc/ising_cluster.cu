@@ -64,8 +64,15 @@ __device__ __forceinline__ int lattice_of_tile(const SwLat* lat, int n, uint32_t
     return lo;
 }
 
-// Bit l of the result = pred of lane l (whole warp).
-__device__ __forceinline__ uint32_t ballot_bit(bool pred) { return __ballot_sync(0xffffffffu, pred); }
+// The 64-bit mask of a tile row in natural order (bit j <-> x0 + j) from each
+// lane's two sites x0 + 2l (bit 0 of v) and x0 + 2l + 1 (bit 1): lanes 0..15
+// fill the low word, lanes 16..31 the high one (two warp OR-reductions).
+__device__ __forceinline__ uint64_t row_mask(uint32_t v, uint32_t lane) {
+    const uint32_t sh = v << (2u * (lane & 15u));
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16u ? sh : 0u);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, lane < 16u ? 0u : sh);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
 
 // The 32 bits of v moved to the even bit positions of a 64-bit word.
 __device__ __forceinline__ uint64_t spread_even(uint32_t v) {
@@ -150,7 +157,8 @@ __device__ __forceinline__ bool unite_global(uint32_t* lab, uint32_t a, uint32_t
 // Bonds and tile-local labels: one warp per tile, rows in order.  Lane l owns
 // the sites x0 + 2l and x0 + 2l + 1 of every row, whose four bond draws are
 // one Philox block (q = p >> 1 with p = y*L + x0 + 2l even).  Row k: the
-// row's right / down bond masks come from two ballots each; every site of a
+// row's right / down bond masks come from two warp OR-reductions each
+// (row_mask); every site of a
 // run of right bonds is labelled by the run's first site; the runs are joined
 // to the runs of row k - 1 through the down bonds of row k - 1 (one union per
 // pair of runs, lanes in parallel).  The tile is flattened at the end by
@@ -196,13 +204,14 @@ __global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwSta
         const uint64_t al_d = ~(row ^ below);
         const uint32_t p = (y0 + k) * L + x0 + xe;
         const uint4 r = philox(p >> 1, t, d.sim, kPhaseBond, d.key0, d.key1);
-        const uint32_t re = ballot_bit(((al_r >> xe) & 1u) && r.x < d.thr);
-        const uint32_t ro = ballot_bit(((al_r >> xo) & 1u) && r.z < d.thr);
-        const uint32_t de = ballot_bit(((al_d >> xe) & 1u) && r.y < d.thr);
-        const uint32_t dd = ballot_bit(((al_d >> xo) & 1u) && r.w < d.thr);
+        const uint32_t vr = (uint32_t)(((al_r >> xe) & 1u) && r.x < d.thr) |
+                            ((uint32_t)(((al_r >> xo) & 1u) && r.z < d.thr) << 1);
+        const uint32_t vd = (uint32_t)(((al_d >> xe) & 1u) && r.y < d.thr) |
+                            ((uint32_t)(((al_d >> xo) & 1u) && r.w < d.thr) << 1);
+        const uint64_t mr = row_mask(vr, lane), md = row_mask(vd, lane);
         if (lane == 0) {
-            s_R[warp][k] = spread_even(re) | (spread_even(ro) << 1);
-            s_D[warp][k] = spread_even(de) | (spread_even(dd) << 1);
+            s_R[warp][k] = mr;
+            s_D[warp][k] = md;
         }
     }
     __syncwarp();
@@ -253,8 +262,7 @@ __global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwSta
         const uint32_t pe = (y0 + k) * L + x0 + xe;
         *reinterpret_cast<uint2*>(glab + pe) = make_uint2((y0 + (re >> 6)) * L + x0 + (re & 63u),
                                                           (y0 + (ro >> 6)) * L + x0 + (ro & 63u));
-        const uint64_t roots = spread_even(ballot_bit(re == i0 + xe)) |
-                               (spread_even(ballot_bit(ro == i0 + xo)) << 1);
+        const uint64_t roots = row_mask((uint32_t)(re == i0 + xe) | ((uint32_t)(ro == i0 + xo) << 1), lane);
         if (lane < 2) sw.coins[(d.site_off + (uint64_t)(y0 + k) * L + x0) / 32 + lane] = (uint32_t)(roots >> (32 * lane));
     }
     if (lane == 0) {
