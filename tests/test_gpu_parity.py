@@ -92,6 +92,27 @@ def test_streaming_kernel_bit_exact(L, V, R, T, cold):
     assert np.array_equal(sim.spins(0), ref)
 
 
+@pytest.mark.parametrize("Ls", [(2048,), (4096,), (1024, 2048, 4096)])
+def test_default_streaming_tiling_bit_exact(Ls):
+    """The streaming plan with the default tiling, which depends on the
+    blocks each candidate gives (on a 152-SM GB300: 1 x 2 for 2048^2, 2 x 2
+    for 4096^2): bit-exact, and the tiling in use is one of the candidates."""
+    n = 3
+    temps = [TC, 1.5, 3.0][:len(Ls)]
+    seeds = [91 + i for i in range(len(Ls))]
+    sim = ising.IsingSim(Ls=list(Ls), temps=temps, seeds=seeds, trace_cap=n)
+    sim.set_plan(ising.ISING_PLAN_STREAM)
+    plan = ising.ising_get_plan(sim.h)
+    assert (plan["words_per_thread"], plan["rows_per_item"]) in {(4, 4), (2, 2), (1, 2), (1, 1)}
+    refs = [oracle.init(L, s_, i, n_threads=NT) for i, (L, s_) in enumerate(zip(Ls, seeds))]
+    sim.sweep(n)
+    Eo, Mo = oracle.sweeps_batch(refs, temps, seeds, list(range(len(refs))), 0, n, NT)
+    Eg, Mg = sim.trace(n)
+    assert np.array_equal(Eg, Eo) and np.array_equal(Mg, Mo)
+    for i in range(len(refs)):
+        assert np.array_equal(sim.spins(i), refs[i]), i
+
+
 @pytest.mark.parametrize("L,k,threads", [(64, 1, 64), (192, 3, 96), (256, 8, 0), (512, 5, 512), (1024, 2, 512)])
 def test_resident_kernel_bit_exact(L, k, threads):
     n = 11
