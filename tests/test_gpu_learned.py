@@ -155,6 +155,14 @@ def test_learned_round_matches_oracle(rnd):
     assert 0 <= acc <= 16
 
 
+def test_learned_round_128_matches_oracle():
+    """128^2: 64 patches, two full groups of 32 (the acceptance kernel's
+    16-byte staging path), against the oracle's whole round."""
+    flat = ol.init_params(17, gain=0.3)
+    acc = _round_compare(128, 3.5, 202, 1, flat)
+    assert 0 <= acc <= 64
+
+
 def test_learned_round_on_batch_keeps_bookkeeping():
     from paper_2404_16990_gb300 import workloads
     wl = workloads.random_batch(5, Ls=(64, 128, 192), tmin=2.0, tmax=4.0, seed=4)
