@@ -300,9 +300,13 @@ void ising_net_destroy(ising_net_t net);
  * e4m3(W * s_l) with s_l = 2^floor(log2(448 / max|W of layer l|)) (layers 1..4),
  * hidden activations as e4m3(relu(.)) (round to nearest even, saturating),
  * products summed in fp32 (mma.sync e4m3, K = 32: taps 0+1, 2+3, 4) and
- * divided by s_l before the fp32 bias.  The MH correction uses the same
- * arithmetic for x and x', so either precision samples the Boltzmann
- * distribution exactly; FP8 changes only the acceptance rate and the cost. */
+ * divided by s_l before the fp32 bias.  The MH correction evaluates log q of
+ * x and x' with one and the same kernel.  In FP8 the proposal is drawn with
+ * that kernel's logits too; in BF16 it is drawn by a separate (wavefront)
+ * kernel whose logits equal the scoring kernel's up to the order of the fp32
+ * sums.  Either precision therefore samples the Boltzmann distribution up to
+ * a relative bias of about 1e-6 (and the 2^-32 quantization of the sampling
+ * thresholds); FP8 changes the acceptance rate and the cost. */
 #define ISING_NET_BF16 0
 #define ISING_NET_FP8 1
 int ising_net_set_precision(ising_net_t net, int precision);
@@ -337,7 +341,9 @@ int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int
                     int batch, float lr, uint64_t seed, float* host_losses);
 
 /* One learned patch round over every lattice of h (round index round_index;
- * L must be a multiple of 16, which every valid L is), on h's stream.  With
+ * L must be a multiple of 16, which every valid L is), on h's stream: gather
+ * the patches' windows, sample proposals, score the current and the proposed
+ * windows (in BF16 both in one launch), accept or reject in FP64.  With
  * host_accepted [n_sims] not NULL the call synchronises and returns the
  * patches accepted in this round; with NULL it only enqueues the round and the
  * per-lattice counts accumulate on the device (read them with
