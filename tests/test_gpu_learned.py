@@ -43,6 +43,24 @@ def test_score_matches_oracle():
     assert np.allclose(lq, lqo, atol=5e-2, rtol=1e-3)
 
 
+def test_score_large_batch_matches_oracle_on_a_subset():
+    """8,000 windows: more than the persistent scoring kernel has warps (4
+    blocks of 4 warps per SM), so warps take several windows; 200 windows, half
+    of them from the tail, against the oracle's forward pass."""
+    B = 8000
+    net = ising.IsingNet(max_windows=B)
+    flat = ol.init_params(23, gain=1.5)
+    net.set_params(flat)
+    win = rand_windows(B, 6)
+    lq, z = net.score(win, with_z=True)
+    pick = sorted(np.random.default_rng(9).choice(7200, 100, replace=False).tolist()) + list(range(B - 100, B))
+    zo, _ = ol.forward(win[pick], flat)
+    inner = ol.interior_mask(10).ravel()
+    dz = np.abs(z[pick][:, inner] - zo.reshape(len(pick), 100)[:, inner])
+    assert np.median(dz) < 1e-4 and dz.max() < 3e-2, (np.median(dz), dz.max())
+    assert np.allclose(lq[pick], ol.log_q(win[pick], zo), atol=5e-2, rtol=1e-3)
+
+
 def test_gradient_matches_oracle():
     net = ising.IsingNet(max_windows=512)
     flat = ol.init_params(9, gain=1.5)
