@@ -48,7 +48,7 @@ def test_score_large_batch_matches_oracle_on_a_subset():
     blocks of 4 warps per SM), so warps take several windows; 200 windows, half
     of them from the tail, against the oracle's forward pass."""
     B = 8000
-    net = ising.IsingNet(max_windows=B)
+    net = ising.IsingNet(max_windows=B, max_batch=B)     # logits of every window: n <= max_batch
     flat = ol.init_params(23, gain=1.5)
     net.set_params(flat)
     win = rand_windows(B, 6)
