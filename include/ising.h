@@ -201,8 +201,9 @@ int ising_state_bytes(ising_t h, size_t* bytes);
 int ising_save(ising_t h, void* host_buf, size_t bytes);
 int ising_load(ising_t h, const void* host_buf, size_t bytes);
 
-/* Execution plan.  ISING_PLAN_AUTO picks the kernel from the lattice sizes
- * (lattices up to L = 1024 stay resident, larger ones stream); the others
+/* Execution plan.  ISING_PLAN_AUTO (the default) streams every lattice with
+ * the default tiling: on GB300 the resident kernel measured at best even with
+ * the streaming one and up to 17x slower (one 1024^2 lattice).  The others
  * force one kernel for every lattice: RESIDENT keeps each lattice (or group
  * of equal-size lattices) in shared memory for many sweeps (up to the
  * shared-memory limit, else ISING_EINVAL); STREAM runs one launch per
@@ -210,10 +211,10 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
  * words_per_thread in {1, 2, 4} = 32-bit words per streaming thread and row;
  * rows_per_item = rows per streaming thread (lowered per lattice so that one tile
  * of a block never spans more rows than the lattice has).  By default the
- * streaming tiling is 4 words and 4 rows per thread, reduced (words first,
- * then rows if rows_per_item is also 0) while the streamed lattices would
- * give fewer blocks than one full wave on the device; ising_get_plan reports
- * the tiling in use.  sweeps_per_unit = sweeps a
+ * streaming tiling follows the number of blocks of 256 threads it gives:
+ * 4 words x 4 rows per thread from 4 blocks per SM, else 2 x 2 from 1.5, else
+ * 1 x 2 from 0.5, else 1 x 1 (rows as given when rows_per_item is set);
+ * ising_get_plan reports the tiling in use.  sweeps_per_unit = sweeps a
  * resident work unit runs before its group is stored; threads = block size
  * (a multiple of 32, at most 512 resident / 256 streaming).  No choice
  * changes any result bit. */
@@ -221,6 +222,9 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
 #define ISING_PLAN_RESIDENT 1
 #define ISING_PLAN_STREAM 2
 #define ISING_PLAN_PERSIST 3
+/* ISING_PLAN_MIXED: lattices with L <= 1024 resident (as RESIDENT, grouped by
+ * size), larger ones streamed (as STREAM), in the same sweeps. */
+#define ISING_PLAN_MIXED 4
 int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int sweeps_per_unit, int threads);
 

@@ -184,10 +184,13 @@ int build_tables(ising_handle* h) {
                 return fail(ISING_EINVAL, "lattice %d (L=%d) does not fit in shared memory (%zu > %zu bytes)",
                             i, h->L[i], bytes, res_budget);
             res = true;
-        } else if (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST) {
-            res = false;
-        } else {
+        } else if (h->plan.mode == ISING_PLAN_MIXED) {
             res = h->L[i] <= 1024 && bytes <= res_budget;
+        } else {
+            // STREAM, PERSIST and AUTO: streamed.  AUTO streams too: on GB300 the
+            // resident kernel measured at best even with the streaming one (one
+            // 64^2 lattice) and up to 17x slower (one 1024^2 lattice)
+            res = false;
         }
         (res ? resident : streamed).push_back(i);
     }
@@ -783,7 +786,7 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int threads) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (plan != ISING_PLAN_AUTO && plan != ISING_PLAN_RESIDENT && plan != ISING_PLAN_STREAM &&
-        plan != ISING_PLAN_PERSIST)
+        plan != ISING_PLAN_PERSIST && plan != ISING_PLAN_MIXED)
         return fail(ISING_EINVAL, "unknown plan %d", plan);
     if (words_per_thread != 0 && words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4)
         return fail(ISING_EINVAL, "words_per_thread must be 0, 1, 2 or 4");
@@ -796,7 +799,7 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
     p.words_per_thread = words_per_thread;
     p.sweeps_per_unit = sweeps_per_unit;
     p.rows_per_item = rows_per_item;
-    if (plan == ISING_PLAN_STREAM || plan == ISING_PLAN_PERSIST) {
+    if (plan == ISING_PLAN_STREAM || plan == ISING_PLAN_PERSIST || plan == ISING_PLAN_AUTO) {
         if (threads != 0 && threads > 256) return fail(ISING_EINVAL, "streaming kernel allows at most 256 threads");
         p.stream_threads = threads ? threads : 256;
     } else {
@@ -879,14 +882,19 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
         int rc = apply_cand(h, cached);
         if (rc == ISING_OK) return ISING_OK;
     }
-    // candidates: resident (lattices up to L = 1024) with several unit sizes
-    // and block sizes, and the streaming kernel with several tilings
+    // candidates: the resident kernel (when every lattice has L <= 1024) with
+    // several unit sizes and block sizes, and the streaming and persistent
+    // kernels with several tilings
     std::vector<TuneCand> cands;
-    bool any_resident = false;
-    for (int L : h->L) any_resident |= (L <= 1024);
-    if (any_resident)
+    bool all_small = true, any_small = false;
+    for (int L : h->L) {
+        all_small &= (L <= 1024);
+        any_small |= (L <= 1024);
+    }
+    if (any_small)
         for (int k : {8, 32, 128})
-            for (int thr : {0, 256, 512}) cands.push_back({ISING_PLAN_AUTO, 0, 4, k, thr});
+            for (int thr : {0, 256, 512})
+                cands.push_back({all_small ? ISING_PLAN_RESIDENT : ISING_PLAN_MIXED, 0, 0, k, thr});
     const int Vs[] = {1, 2, 4};
     for (int V : Vs) {
         bool ok = true;
@@ -953,7 +961,8 @@ int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_it
     if (rows_per_item) *rows_per_item = h->R;
     if (sweeps_per_unit) *sweeps_per_unit = h->plan.sweeps_per_unit;
     if (threads)
-        *threads = (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST) ? h->plan.stream_threads
+        *threads = (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST ||
+                    h->plan.mode == ISING_PLAN_AUTO) ? h->plan.stream_threads
                                                                                              : h->res_threads;
     return ISING_OK;
 }

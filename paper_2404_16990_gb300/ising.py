@@ -31,6 +31,7 @@ ISING_PLAN_AUTO = 0
 ISING_PLAN_RESIDENT = 1
 ISING_PLAN_STREAM = 2
 ISING_PLAN_PERSIST = 3
+ISING_PLAN_MIXED = 4
 ISING_MIN_L = 64
 ISING_MAX_L = 65536
 

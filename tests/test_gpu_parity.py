@@ -156,7 +156,8 @@ def test_uneven_batch_bit_exact(plan, kw):
 def test_mixed_resident_and_streamed_batch():
     wl = workloads.random_batch(9, Ls=(64, 128, 2048), seed=3)
     assert 2048 in wl.Ls and min(wl.Ls) < 1024
-    _batch_check(wl, 9)
+    _batch_check(wl, 9, ising.ISING_PLAN_MIXED)
+    _batch_check(wl, 5)         # the default plan streams every lattice
 
 
 def test_batch754_sample_and_prefix():
