@@ -69,12 +69,12 @@ __device__ __forceinline__ int lattice_of_item(const Lat3* lat, int n, uint64_t 
 // 2 acc + [r >= t] by the carry of r - t, as in the 2D sweep (madc for the
 // shift-in: 0.6 % faster at 1024^3, 3-4 % at 256^3 and 512^3).
 __device__ __forceinline__ uint32_t shift_in_not_below3(uint32_t acc, uint32_t r, uint32_t t) {
-    uint32_t diff, out;
-    asm("sub.cc.u32 %0, %2, %3;\n\t"
-        "madc.lo.u32 %1, %4, 2, 0;"
-        : "=r"(diff), "=r"(out)
+    uint32_t out;
+    asm("{\n\t.reg .u32 d;\n\t"
+        "sub.cc.u32 d, %1, %2;\n\t"
+        "madc.lo.u32 %0, %3, 2, 0;\n\t}"
+        : "=r"(out)
         : "r"(r), "r"(t), "r"(acc));
-    (void)diff;
     return out;
 }
 

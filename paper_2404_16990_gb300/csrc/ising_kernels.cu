@@ -59,12 +59,12 @@ struct SiteKey {
 // addc: the same result and instruction count; the sweep measured 1.5 %
 // faster with it, the kernel at 124 instead of 128 registers.)
 __device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t r, uint32_t t) {
-    uint32_t diff, out;
-    asm("sub.cc.u32 %0, %2, %3;\n\t"
-        "madc.lo.u32 %1, %4, 2, 0;"
-        : "=r"(diff), "=r"(out)
+    uint32_t out;
+    asm("{\n\t.reg .u32 d;\n\t"
+        "sub.cc.u32 d, %1, %2;\n\t"
+        "madc.lo.u32 %0, %3, 2, 0;\n\t}"
+        : "=r"(out)
         : "r"(r), "r"(t), "r"(acc));
-    (void)diff;
     return out;
 }
 
