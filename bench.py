@@ -37,7 +37,7 @@ SM_MAX_MHZ = 2070.0
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch of that kernel build, from an ncu full
 # capture (first captured launch); other pairings report null
-MEASURED_TRAFFIC = {("l16384", "stream_half_kernel<4>", 3 * 16384 * 16384 // 2): 110_439_680}
+MEASURED_TRAFFIC = {("l16384", "stream_half_kernel<4>", 3 * 16384 * 16384 // 2): 110_270_720}
 
 
 def parse():
