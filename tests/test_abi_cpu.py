@@ -46,6 +46,23 @@ def test_library_exports_every_declared_symbol():
     assert set(_declared_functions()) <= exported
 
 
+def test_python_constants_match_the_header():
+    """Every integer #define ISING_* of include/ising.h that the binding
+    mirrors has the same value there (the binding passes them to the ABI)."""
+    defines = {}
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define\s+(ISING_[A-Z0-9_]+)\s+\(?(-?[0-9]+)\)?\s*$", open(hdr).read(), flags=re.M):
+            defines[m.group(1)] = int(m.group(2))
+    mirrored = {k: v for k, v in vars(ising).items() if k.startswith("ISING_") and isinstance(v, int)}
+    assert mirrored, "the binding mirrors no constants"
+    for name, value in mirrored.items():
+        if name in defines:
+            assert defines[name] == value, (name, defines[name], value)
+    for name in ("ISING_PLAN_AUTO", "ISING_PLAN_RESIDENT", "ISING_PLAN_STREAM", "ISING_PLAN_PERSIST",
+                 "ISING_PLAN_MIXED", "ISING_NET_BF16", "ISING_NET_FP8"):
+        assert name in defines and name in mirrored, name
+
+
 def test_library_has_no_oracle_dependency():
     # the product library links nothing from oracle/
     lib_path = ising._build.build()
