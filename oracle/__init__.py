@@ -10,7 +10,8 @@ method's arithmetic) serve both sides.
 The arithmetic lives in ``ising_oracle.c`` (plain C, one byte per spin, the
 definitions of Section 1 and Algorithm 5 written out site by site) and
 ``cluster_oracle.c`` (the Swendsen-Wang cluster step named in Section 1) and
-``ising3d_oracle.c`` (the same sweep on the simple cubic lattice);
+``ising3d_oracle.c`` (the same sweep on the simple cubic lattice) and
+``wolff_oracle.c`` (the Wolff single-cluster step);
 this module compiles them with gcc and wraps them with ctypes and numpy.
 """
 from __future__ import annotations
@@ -24,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
-_SOURCES = ("ising_oracle.c", "cluster_oracle.c", "ising3d_oracle.c")
+_SOURCES = ("ising_oracle.c", "cluster_oracle.c", "ising3d_oracle.c", "wolff_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -112,6 +113,18 @@ def _load():
                                                ctypes.c_uint32, ctypes.c_int64, i64p, i64p,
                                                ctypes.c_int]
         lib.oracle_sw_sweeps_batch.restype = ctypes.c_int
+        lib.oracle_wolff_seed.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_wolff_seed.restype = ctypes.c_uint32
+        lib.oracle_wolff_step.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.c_uint32]
+        lib.oracle_wolff_step.restype = ctypes.c_int64
+        lib.oracle_wolff_steps.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_uint32, ctypes.c_int64, i64p, i64p, i64p]
+        lib.oracle_wolff_steps.restype = ctypes.c_int
+        lib.oracle_wolff_steps_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(i8p), u32p, ctypes.POINTER(ctypes.c_uint64),
+                                                 u32p, ctypes.c_uint32, ctypes.c_int64, i64p, i64p, ctypes.c_int]
+        lib.oracle_wolff_steps_batch.restype = ctypes.c_int
         lib.oracle3d_thresholds.argtypes = [ctypes.c_double, u32p]
         lib.oracle3d_thresholds.restype = ctypes.c_int
         lib.oracle3d_init.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i8p]
@@ -334,6 +347,46 @@ def energy3d(sigma: np.ndarray) -> int:
 def magnetization3d(sigma: np.ndarray) -> int:
     sigma = np.ascontiguousarray(sigma, dtype=np.int8)
     return int(_load().oracle3d_magnetization(sigma.shape[0], _ptr(sigma, ctypes.c_int8)))
+
+
+def wolff_seed(L: int, seed: int, s: int, t: int) -> int:
+    """The seed site p = y*L + x of Wolff step t."""
+    return int(_load().oracle_wolff_seed(L, seed, s, t))
+
+
+def wolff_sweeps(sigma: np.ndarray, T: float, seed: int, s: int, t0: int, n: int):
+    """In place: n Wolff steps with indices t0..t0+n-1.  Returns the (E, M)
+    traces and the cluster sizes."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    E = np.zeros(max(n, 0), dtype=np.int64)
+    M = np.zeros(max(n, 0), dtype=np.int64)
+    C = np.zeros(max(n, 0), dtype=np.int64)
+    rc = _load().oracle_wolff_steps(sigma.shape[0], _ptr(sigma, ctypes.c_int8), sw_threshold(T), seed, s, t0, n,
+                                    _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), _ptr(C, ctypes.c_int64))
+    if rc != 0:
+        raise MemoryError("oracle_wolff_steps: allocation failed")
+    return E, M, C
+
+
+def wolff_sweeps_batch(sigmas, temps, seeds, sims, t0: int, n: int, n_threads: int = 1):
+    """In place over a list of int8 lattices.  Returns traces [n_lat, n]."""
+    n_lat = len(sigmas)
+    Ls = np.array([x.shape[0] for x in sigmas], dtype=np.int32)
+    thr = np.array([sw_threshold(T) for T in temps], dtype=np.uint32)
+    seeds_a = np.array([int(x) for x in seeds], dtype=np.uint64)
+    sims_a = np.array([int(x) for x in sims], dtype=np.uint32)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * max(n_lat, 1))()
+    for j, x in enumerate(sigmas):
+        assert x.dtype == np.int8 and x.flags.c_contiguous
+        ptrs[j] = _ptr(x, ctypes.c_int8)
+    E = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    M = np.zeros((n_lat, max(n, 0)), dtype=np.int64)
+    rc = _load().oracle_wolff_steps_batch(n_lat, _ptr(Ls, ctypes.c_int), ptrs, _ptr(thr, ctypes.c_uint32),
+                                          _ptr(seeds_a, ctypes.c_uint64), _ptr(sims_a, ctypes.c_uint32), t0, n,
+                                          _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), n_threads)
+    if rc != 0:
+        raise MemoryError("oracle_wolff_steps_batch: allocation failed")
+    return E, M
 
 
 def sweeps3d(sigma: np.ndarray, T: float, seed: int, s: int, t0: int, n: int):

@@ -157,3 +157,51 @@ def test_3d_unmodified_source_passes_same_checks(tmp_path):
     so = oracle.compile_variant(oracle.source_text("ising3d_oracle.c"), str(tmp_path), "o3d_clean",
                                 which="ising3d_oracle.c")
     assert _caught_3d(so) == []
+
+# --------------------------------------------------------------------------
+# The same for the Wolff oracle (wolff_oracle.c).
+# --------------------------------------------------------------------------
+import test_wolff_oracle as wpins  # noqa: E402
+
+WOLFF_MUTATIONS = {
+    "wolff_unequal_spins": ("if (in[j] || sigma[j] != s0) continue;", "if (in[j]) continue;"),
+    "wolff_bonds_ignored": ("if (!wolff_bond_active(seed, s, t, thr, owner[k], dir[k])) continue;", ""),
+    "wolff_own_draw_for_left_and_up": ("const uint32_t owner[4] = { p, left, p, up };",
+                                       "const uint32_t owner[4] = { p, p, p, p };"),
+    "wolff_same_lane_both_bonds": ("2u * (p & 1u) + (uint32_t)dir", "2u * (p & 1u)"),
+    "wolff_seed_mapping": ("return (uint32_t)((r * (uint64_t)L * (uint64_t)L) >> 32);",
+                           "return (uint32_t)(r % ((uint64_t)L * (uint64_t)L));"),
+}
+
+
+def _caught_wolff(variant_so) -> list:
+    caught = []
+    with oracle.use_library(variant_so):
+        checks = [
+            ("component", lambda: wpins.test_wolff_step_is_the_seed_component(8, 1.5, 11)),
+            ("chi2_4x4", lambda: wpins.test_wolff_4x4_joint_distribution_matches_enumeration(exact.T_C)),
+            ("kaufman", lambda: wpins.test_wolff_energy_matches_kaufman(exact.T_C)),
+            ("t0", wpins.test_wolff_zero_temperature_flips_the_domain),
+            ("t_inf", wpins.test_wolff_infinite_temperature_flips_one_site),
+        ]
+        for name, fn in checks:
+            try:
+                fn()
+            except AssertionError:
+                caught.append(name)
+    return caught
+
+
+@pytest.mark.parametrize("name", sorted(WOLFF_MUTATIONS))
+def test_wolff_pins_catch_planted_mistake(name, tmp_path):
+    old, new = WOLFF_MUTATIONS[name]
+    src = oracle.source_text("wolff_oracle.c")
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    so = oracle.compile_variant(src.replace(old, new), str(tmp_path), "wolff_" + name, which="wolff_oracle.c")
+    assert _caught_wolff(so), f"no pin caught the planted mistake {name}"
+
+
+def test_wolff_unmodified_source_passes_same_checks(tmp_path):
+    so = oracle.compile_variant(oracle.source_text("wolff_oracle.c"), str(tmp_path), "wolff_clean",
+                                which="wolff_oracle.c")
+    assert _caught_wolff(so) == []
