@@ -437,7 +437,27 @@ int ising_sw_get_thresholds(ising_t h, uint32_t* thr);
  * makes the next synchronising call return ISING_ETIMEOUT. */
 int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes);
 
-/* Cluster labels of lattice `sim` for the step the handle would take next
+/* Advance every lattice by n >= 0 Wolff single-cluster steps (Wolff, PRL 62,
+ * 361 (1989)): a seed site is chosen, its cluster grown over nearest
+ * neighbours of equal spin joined by active bonds, and flipped.  Draws
+ * (Philox4x32-10 keyed by the lattice's seed, counter (q, t, s, phase), t =
+ * the step's index in the handle's sweep counter, s = simulation index):
+ *   seed, phase 9: r = lane 0 of block q = 0; the seed is site
+ *     p0 = floor(r L^2 / 2^32) (p = y*L + x);
+ *   bonds, phase 10: site p owns the bonds to (x+1, y) and (x, y+1); q =
+ *     p >> 1, lane 2*(p & 1) is the right bond's draw, lane 2*(p & 1) + 1 the
+ *     down bond's; a bond is active iff its draw is below the Swendsen-Wang
+ *     bond threshold (ising_sw_get_thresholds).
+ * With one draw per bond, each bond is tried at most once and the cluster is
+ * the seed's connected component among equal spins joined by active bonds.
+ * Scratch as for ising_sw_sweep (same size, same rules).  Asynchronous on the
+ * handle's stream: one launch for all n steps of every lattice (a block per
+ * lattice); after each step E and M are recorded exactly as after a sweep and
+ * the sweep counter advances by one.  Steps, Swendsen-Wang steps and
+ * Metropolis sweeps share the counter and may be mixed. */
+int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes);
+
+/* Cluster labels of lattice `sim` for the step the handle would take next/* Cluster labels of lattice `sim` for the step the handle would take next
  * (its current sweep counter), without taking it: host_labels[L*L]
  * (caller-owned) receives, for every site p = y*L + x, the smallest site
  * index of its cluster.  Synchronises the stream.  The spins and the sweep

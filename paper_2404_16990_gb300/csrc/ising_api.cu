@@ -1145,6 +1145,25 @@ int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes
     return ISING_OK;
 }
 
+int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
+    if (h->n == 0) return ISING_OK;
+    if (h->t + n > (int64_t)0xFFFFFFFFll)
+        return fail(ISING_EINVAL, "sweep counter would pass 2^32 (Philox counter word 1)");
+    SwState sw{};
+    int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
+    if (rc != ISING_OK || n == 0) return rc;
+    // the visited bits (the coin region of the scratch) start at zero; each
+    // step clears the bits it set
+    CUDA_TRY(cudaMemsetAsync(sw.coins, 0, (size_t)(h->sw_sites / 8), h->stream), "clear visited bits");
+    CUDA_TRY(launch_wolff(h->st, sw, n, h->stream), "Wolff steps");
+    CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
+    h->t += n;
+    h->launches += 2;
+    return ISING_OK;
+}
+
 int ising_sw_labels(ising_t h, int sim, void* dev_scratch, size_t scratch_bytes, uint32_t* host_labels) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (sim < 0 || sim >= h->n) return fail(ISING_EINVAL, "sim %d out of range", sim);

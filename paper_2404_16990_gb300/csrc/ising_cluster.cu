@@ -433,6 +433,127 @@ __global__ void sw_record_kernel(DevState st, int n_lat) {
     if (threadIdx.x == 0) st.ctl->t = t + 1;
 }
 
+// ---------------------------------------------------------------------------
+// Wolff single-cluster step (Wolff 1989), every lattice at once, one block
+// per lattice and all steps of a call in one launch.  Draws: the seed site is
+// floor(r L^2 / 2^32), r = lane 0 of block 0, phase 9; site p owns its right
+// and down bonds, whose draws are lanes 2(p & 1) and 2(p & 1) + 1 of block
+// p >> 1, phase 10, active iff below the Swendsen-Wang bond threshold.  With
+// one draw per bond the cluster is the seed's connected component among
+// equal spins joined by active bonds, so a parallel breadth-first growth
+// finds exactly the cluster of a sequential one.  Per step: levels of the
+// growth (the queue in the label scratch, a visited bit per site in the coin
+// scratch, claimed by atomicOr); then the energy change from the bonds
+// leaving the cluster, the flips (atomicXor on the packed words), the visited
+// bits cleared, E and M recorded.  Every loop is bounded by L^2.
+// ---------------------------------------------------------------------------
+constexpr int kWolffThreads = 512;
+constexpr uint32_t kPhaseWolffSeed = 9u, kPhaseWolffBond = 10u;
+
+// Spin bit (1 = -1) of site (x, y) of a packed lattice, and a visited bit.
+// Both are read from L2 (__ldcg): the flips and the claims are atomics, which
+// act in L2, and an L1 line read earlier in the launch could be stale.
+__device__ __forceinline__ uint32_t site_bit(const uint32_t* words, uint32_t L, uint32_t wn, uint32_t x, uint32_t y) {
+    const uint32_t c = (x + y) & 1u, j = x >> 1;
+    return (__ldcg(&words[((size_t)c * L + y) * wn + (j >> 5)]) >> (j & 31u)) & 1u;
+}
+__device__ __forceinline__ bool visited(const uint32_t* vis, uint32_t v) {
+    return (__ldcg(&vis[v >> 5]) >> (v & 31u)) & 1u;
+}
+
+__global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, SwState sw, long long n_steps) {
+    __shared__ uint32_t s_tail, s_b0;
+    __shared__ long long s_acc[kWolffThreads / 32];
+    if ((int)blockIdx.x >= sw.n) return;
+    const uint32_t lat = blockIdx.x;
+    const SwLat d = sw.lat[lat];
+    const uint32_t L = d.L, wn = d.wn;
+    const uint64_t N = (uint64_t)L * L;
+    uint32_t* queue = sw.label + d.site_off;           // up to L^2 sites
+    uint32_t* vis = sw.coins + d.site_off / 32;        // one bit per site, zero between steps
+    uint32_t* words = st.spins + d.word_off;
+    const unsigned long long t0 = st.ctl->t;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    for (long long step = 0; step < n_steps; ++step) {
+        const uint32_t t = (uint32_t)(t0 + (unsigned long long)step);
+        if (tid == 0) {
+            const uint32_t r = philox(0u, t, d.sim, kPhaseWolffSeed, d.key0, d.key1).x;
+            const uint32_t p0 = (uint32_t)(((uint64_t)r * N) >> 32);
+            s_b0 = site_bit(words, L, wn, p0 % L, p0 / L);
+            queue[0] = p0;
+            atomicOr(&vis[p0 >> 5], 1u << (p0 & 31u));
+            s_tail = 1;
+        }
+        __syncthreads();
+        const uint32_t b0 = s_b0;
+        uint32_t head = 0, tail = 1;
+        // the growth, level by level
+        for (uint64_t level = 0; level < N && head < tail; ++level) {
+            for (uint32_t k = head + tid; k < tail; k += kWolffThreads) {
+                const uint32_t p = __ldcg(&queue[k]);
+                const uint32_t y = p / L, x = p - y * L;
+                const uint32_t xr = (x + 1 == L) ? 0u : x + 1, xl = (x == 0) ? L - 1 : x - 1;
+                const uint32_t yd = (y + 1 == L) ? 0u : y + 1, yu = (y == 0) ? L - 1 : y - 1;
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {                // right, left, down, up
+                    const uint32_t vx = n == 0 ? xr : (n == 1 ? xl : x), vy = n == 2 ? yd : (n == 3 ? yu : y);
+                    const uint32_t v = vy * L + vx;
+                    if (site_bit(words, L, wn, vx, vy) != b0) continue;
+                    if (visited(vis, v)) continue;                           // already claimed (re-checked below)
+                    // the bond's owner: this site for right / down, the neighbour for left / up
+                    const uint32_t owner = (n == 0 || n == 2) ? p : v, dir = (n < 2) ? 0u : 1u;
+                    const uint4 r4 = philox(owner >> 1, t, d.sim, kPhaseWolffBond, d.key0, d.key1);
+                    // lane 2 (owner & 1) + dir, by two-way selects
+                    const uint32_t r = (owner & 1u) ? (dir ? r4.w : r4.z) : (dir ? r4.y : r4.x);
+                    if (r >= d.thr) continue;
+                    const uint32_t bit = 1u << (v & 31u);
+                    if (atomicOr(&vis[v >> 5], bit) & bit) continue;
+                    queue[atomicAdd(&s_tail, 1u)] = v;
+                }
+            }
+            __syncthreads();
+            head = tail;
+            tail = s_tail;
+            __syncthreads();          // every thread has read the tail before the next level grows it
+        }
+        // energy change: 2 * sum over bonds leaving the cluster of sigma_0 sigma_v
+        long long acc = 0;
+        for (uint32_t k = tid; k < tail; k += kWolffThreads) {
+            const uint32_t p = __ldcg(&queue[k]);
+            const uint32_t y = p / L, x = p - y * L;
+            const uint32_t xr = (x + 1 == L) ? 0u : x + 1, xl = (x == 0) ? L - 1 : x - 1;
+            const uint32_t yd = (y + 1 == L) ? 0u : y + 1, yu = (y == 0) ? L - 1 : y - 1;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                const uint32_t vx = n == 0 ? xr : (n == 1 ? xl : x), vy = n == 2 ? yd : (n == 3 ? yu : y);
+                const uint32_t v = vy * L + vx;
+                if (visited(vis, v)) continue;
+                acc += (site_bit(words, L, wn, vx, vy) == b0) ? 1 : -1;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_acc[warp] = acc;
+        __syncthreads();
+        // flips and visited bits cleared
+        for (uint32_t k = tid; k < tail; k += kWolffThreads) {
+            const uint32_t p = __ldcg(&queue[k]);
+            const uint32_t y = p / L, x = p - y * L;
+            const uint32_t c = (x + y) & 1u, j = x >> 1;
+            atomicXor(&words[((size_t)c * L + y) * wn + (j >> 5)], 1u << (j & 31u));
+            atomicAnd(&vis[p >> 5], ~(1u << (p & 31u)));
+        }
+        if (tid == 0) {
+            long long de = 0;
+            for (int w = 0; w < kWolffThreads / 32; ++w) de += s_acc[w];
+            const long long E = st.obs[2 * lat] + 2 * de;
+            const long long M = st.obs[2 * lat + 1] + (b0 ? 2ll : -2ll) * (long long)tail;
+            record_em(st, lat, L, E, M, t0 + (unsigned long long)step);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream_t stream) {
@@ -466,6 +587,12 @@ cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t s
 cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream) {
     if (n_lat <= 0) return cudaSuccess;
     sw_record_kernel<<<1, 256, 0, stream>>>(st, n_lat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, cudaStream_t stream) {
+    if (sw.n <= 0 || n_steps <= 0) return cudaSuccess;
+    wolff_kernel<<<sw.n, kWolffThreads, 0, stream>>>(st, sw, (long long)n_steps);
     return cudaGetLastError();
 }
 

@@ -177,6 +177,9 @@ cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream
 cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t stream);
 cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream);
 cudaError_t launch_sw_compress(const SwState& sw, cudaStream_t stream);   // labels -> final roots
+// Wolff single-cluster steps of every lattice (ising_cluster.cu); the scratch
+// of the cluster step serves as queue (labels) and visited bits (coins).
+cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, cudaStream_t stream);
 
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);

@@ -139,6 +139,7 @@ def _load():
             "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
             "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
+            "ising_wolff_sweep": ([vp, i64, vp, sz], ctypes.c_int),
             "ising_sw_labels": ([vp, ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -526,6 +527,10 @@ def ising_sw_sweep(h, n: int, dev_scratch: int, nbytes: int) -> None:
     _check(_load().ising_sw_sweep(h, n, dev_scratch, nbytes))
 
 
+def ising_wolff_sweep(h, n: int, dev_scratch: int, nbytes: int) -> None:
+    _check(_load().ising_wolff_sweep(h, n, dev_scratch, nbytes))
+
+
 def ising_sw_labels(h, sim: int, dev_scratch: int, nbytes: int) -> np.ndarray:
     L = ising_lattice_size(h, sim)
     lab = np.zeros((max(L, 1), max(L, 1)), dtype=np.uint32)
@@ -609,6 +614,12 @@ class IsingSim:
     def sw_labels(self, sim: int = 0) -> np.ndarray:
         ptr, nbytes = self._sw_scratch()
         return ising_sw_labels(self.h, sim, ptr, nbytes)
+
+    def wolff_sweep(self, n: int) -> None:
+        """n Wolff single-cluster steps of every lattice (the cluster step's
+        scratch, allocated once, on first use)."""
+        ptr, nbytes = self._sw_scratch()
+        ising_wolff_sweep(self.h, n, ptr, nbytes)
 
     def sw_thresholds(self) -> np.ndarray:
         return ising_sw_get_thresholds(self.h)

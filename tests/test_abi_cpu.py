@@ -131,5 +131,6 @@ def test_null_handle_calls_fail_cleanly():
     sz = ctypes.c_size_t()
     assert lib.ising_sw_scratch_bytes(None, ctypes.byref(sz)) == ising.ISING_EINVAL
     assert lib.ising_sw_sweep(None, 1, None, 0) == ising.ISING_EINVAL
+    assert lib.ising_wolff_sweep(None, 1, None, 0) == ising.ISING_EINVAL
     assert lib.ising_sw_labels(None, 0, None, 0, None) == ising.ISING_EINVAL
     assert lib.ising_sw_get_thresholds(None, None) == ising.ISING_EINVAL

@@ -3,7 +3,9 @@ the CPU oracle: bond thresholds, cluster labels (the unique partition with
 minimum-index roots), whole steps bit for bit on uneven batches, steps mixed
 with Metropolis sweeps, graph replay, lattices whose clusters span many tiles
 (up to 4096^2 in full), sampled sites of 16384^2 and 32768^2 lattices, the
-T -> 0 / T -> inf limits, and the API's errors."""
+T -> 0 / T -> inf limits, and the API's errors; and the same for the Wolff
+single-cluster step (uneven batches, cold and random starts, steps mixed with
+sweeps and Swendsen-Wang steps, a 2048^2 lattice at T_c, the limits)."""
 from __future__ import annotations
 
 import numpy as np
@@ -199,3 +201,83 @@ def test_sw_errors():
         ising.ising_sw_scratch_bytes(huge.h)
     assert e.value.code == ising.ISING_EINVAL
     huge.close()
+
+
+# --------------------------------------------------------------------------
+# Wolff single-cluster step
+# --------------------------------------------------------------------------
+def test_wolff_steps_bit_exact_uneven_batch():
+    Ls = [64, 128, 64, 256, 192, 64, 320]
+    temps = [TC, 1.5, 0.5, 3.0, TC, 1e3, 2.1]
+    seeds = [21, 22, 23, 24, 25, 26, 27]
+    n = 25
+    for cold in (False, True):
+        sim = ising.IsingSim(Ls=Ls, temps=temps, seeds=seeds, cold=cold, trace_cap=n)
+        sim.wolff_sweep(n)
+        Eg, Mg = sim.trace(n)
+        for i, (L, T, sd) in enumerate(zip(Ls, temps, seeds)):
+            ref = _oracle_start(L, sd, i, cold)
+            Eo, Mo, _ = oracle.wolff_sweeps(ref, T, sd, i, 0, n)
+            assert np.array_equal(sim.spins(i), ref), (i, L, T, cold)
+            assert np.array_equal(Eg[i], Eo) and np.array_equal(Mg[i], Mo), (i, L, T, cold)
+        assert sim.sweeps_done == n
+        sim.close()
+
+
+def test_wolff_mixed_with_sweeps_and_sw_steps():
+    L, T, seed = 256, TC, 78
+    sim = ising.IsingSim(L, [T], seed, trace_cap=16)
+    ref = oracle.init(L, seed, 0)
+    t = 0
+    for kind, k in (("mp", 2), ("wolff", 4), ("sw", 2), ("wolff", 3), ("mp", 1), ("wolff", 1)):
+        if kind == "mp":
+            sim.sweep(k)
+            Eo, Mo = oracle.sweeps(ref, T, seed, 0, t, k)
+        elif kind == "sw":
+            sim.sw_sweep(k)
+            Eo, Mo = oracle.sw_sweeps(ref, T, seed, 0, t, k)
+        else:
+            sim.wolff_sweep(k)
+            Eo, Mo, _ = oracle.wolff_sweeps(ref, T, seed, 0, t, k)
+        t += k
+        Eg, Mg = sim.trace(k)
+        assert np.array_equal(Eg[0], Eo) and np.array_equal(Mg[0], Mo), (kind, t)
+        assert np.array_equal(sim.spins(0), ref), (kind, t)
+    sim.close()
+
+
+def test_wolff_2048_at_tc_bit_exact():
+    L, T, seed, n = 2048, TC, 5, 6
+    sim = ising.IsingSim(L, [T], seed, trace_cap=n)
+    sim.sweep(20)
+    ref = sim.spins(0)
+    sim.wolff_sweep(n)
+    Eo, Mo, C = oracle.wolff_sweeps(ref, T, seed, 0, 20, n)
+    Eg, Mg = sim.trace(n)
+    assert np.array_equal(sim.spins(0), ref)
+    assert np.array_equal(Eg[0], Eo) and np.array_equal(Mg[0], Mo)
+    assert C.max() > 1
+
+
+def test_wolff_limits():
+    # T -> 0 from a cold start: the whole lattice every step; T -> inf: one site
+    L = 128
+    sim = ising.IsingSim(L, [0.01, 1e9], 3, cold=True, trace_cap=4)
+    sim.wolff_sweep(4)
+    E, M = sim.trace(4)
+    assert list(M[0]) == [-(L * L), L * L, -(L * L), L * L]
+    assert np.all(E[0] == -2 * L * L)
+    dM = np.diff(np.concatenate([[L * L], M[1]]))
+    assert set(np.abs(dM).tolist()) == {2}              # one site per step
+    assert np.count_nonzero(sim.spins(1) == -1) <= 4
+    sim.close()
+
+
+def test_wolff_scratch_errors():
+    sim = ising.IsingSim(64, [TC], 1)
+    with pytest.raises(ising.IsingError):
+        ising.ising_wolff_sweep(sim.h, 1, 0, 0)          # no scratch
+    with pytest.raises(ising.IsingError):
+        sim.wolff_sweep(-1)
+    sim.close()
+
