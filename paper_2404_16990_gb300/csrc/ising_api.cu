@@ -1157,7 +1157,13 @@ int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_by
     // the visited bits (the coin region of the scratch) start at zero; each
     // step clears the bits it set
     CUDA_TRY(cudaMemsetAsync(sw.coins, 0, (size_t)(h->sw_sites / 8), h->stream), "clear visited bits");
-    CUDA_TRY(launch_wolff(h->st, sw, n, h->stream), "Wolff steps");
+    uint32_t max_small = 0;
+    bool any_large = false;
+    for (int L : h->L) {
+        if ((uint32_t)L <= wolff_smem_max_L()) max_small = std::max(max_small, (uint32_t)L);
+        else any_large = true;
+    }
+    CUDA_TRY(launch_wolff(h->st, sw, n, max_small, any_large, h->stream), "Wolff steps");
     CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
     h->t += n;
     h->launches += 2;

@@ -442,55 +442,106 @@ __global__ void sw_record_kernel(DevState st, int n_lat) {
 // one draw per bond the cluster is the seed's connected component among
 // equal spins joined by active bonds, so a parallel breadth-first growth
 // finds exactly the cluster of a sequential one.  Per step: levels of the
-// growth (the queue in the label scratch, a visited bit per site in the coin
-// scratch, claimed by atomicOr); then the energy change from the bonds
-// leaving the cluster, the flips (atomicXor on the packed words), the visited
-// bits cleared, E and M recorded.  Every loop is bounded by L^2.
+// growth (a queue of sites, a visited bit per site claimed by atomicOr); then
+// the energy change from the bonds leaving the cluster, the flips (atomicXor
+// on the packed words), the visited bits cleared, E and M recorded.  Every
+// loop is bounded by L^2.
+//
+// The growth is a chain of dependent steps (a site is found only after its
+// parent), so the latency of each hop sets the time.  Lattices with
+// L <= kWolffSmemMaxL run entirely in shared memory (packed spins, visited
+// bits, a queue of 16-bit site indices: 2.25 L^2 bytes, 144 KB at 256^2),
+// loaded once per call and written back at its end; larger ones keep the
+// queue in the cluster scratch's labels and the visited bits in its coins,
+// and read spins, visited bits and queue from L2 (__ldcg): the flips and the
+// claims are atomics, which act in L2, and an L1 line read earlier in the
+// launch could be stale.
 // ---------------------------------------------------------------------------
 constexpr int kWolffThreads = 512;
+constexpr uint32_t kWolffSmemMaxL = 256;
 constexpr uint32_t kPhaseWolffSeed = 9u, kPhaseWolffBond = 10u;
 
-// Spin bit (1 = -1) of site (x, y) of a packed lattice, and a visited bit.
-// Both are read from L2 (__ldcg): the flips and the claims are atomics, which
-// act in L2, and an L1 line read earlier in the launch could be stale.
-__device__ __forceinline__ uint32_t site_bit(const uint32_t* words, uint32_t L, uint32_t wn, uint32_t x, uint32_t y) {
-    const uint32_t c = (x + y) & 1u, j = x >> 1;
-    return (__ldcg(&words[((size_t)c * L + y) * wn + (j >> 5)]) >> (j & 31u)) & 1u;
-}
-__device__ __forceinline__ bool visited(const uint32_t* vis, uint32_t v) {
-    return (__ldcg(&vis[v >> 5]) >> (v & 31u)) & 1u;
-}
+template <bool SMEM>
+struct WolffStore {
+    uint32_t* words;      // packed spins of the lattice
+    uint32_t* vis;        // visited bits
+    uint32_t* q32;        // queue (global)
+    uint16_t* q16;        // queue (shared)
+    uint32_t L, wn;
+    __device__ __forceinline__ uint32_t load(const uint32_t* a) const { return SMEM ? *a : __ldcg(a); }
+    __device__ __forceinline__ uint32_t word_index(uint32_t x, uint32_t y) const {
+        return ((x + y) & 1u) * L * wn + y * wn + (x >> 6);
+    }
+    __device__ __forceinline__ uint32_t spin(uint32_t x, uint32_t y) const {
+        return (load(&words[word_index(x, y)]) >> ((x >> 1) & 31u)) & 1u;
+    }
+    __device__ __forceinline__ bool visited(uint32_t v) const { return (load(&vis[v >> 5]) >> (v & 31u)) & 1u; }
+    __device__ __forceinline__ bool claim(uint32_t v) {      // true if this call set the bit
+        const uint32_t bit = 1u << (v & 31u);
+        return !(atomicOr(&vis[v >> 5], bit) & bit);
+    }
+    __device__ __forceinline__ void unclaim(uint32_t v) { atomicAnd(&vis[v >> 5], ~(1u << (v & 31u))); }
+    __device__ __forceinline__ uint32_t get(uint32_t k) const { return SMEM ? (uint32_t)q16[k] : __ldcg(&q32[k]); }
+    __device__ __forceinline__ void put(uint32_t k, uint32_t v) {
+        if (SMEM) q16[k] = (uint16_t)v;
+        else q32[k] = v;
+    }
+    __device__ __forceinline__ void flip(uint32_t x, uint32_t y) {
+        atomicXor(&words[word_index(x, y)], 1u << ((x >> 1) & 31u));
+    }
+};
 
+template <bool SMEM>
 __global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, SwState sw, long long n_steps) {
+    extern __shared__ __align__(16) uint32_t wolff_smem[];
     __shared__ uint32_t s_tail, s_b0;
     __shared__ long long s_acc[kWolffThreads / 32];
     if ((int)blockIdx.x >= sw.n) return;
     const uint32_t lat = blockIdx.x;
     const SwLat d = sw.lat[lat];
     const uint32_t L = d.L, wn = d.wn;
-    const uint64_t N = (uint64_t)L * L;
-    uint32_t* queue = sw.label + d.site_off;           // up to L^2 sites
-    uint32_t* vis = sw.coins + d.site_off / 32;        // one bit per site, zero between steps
-    uint32_t* words = st.spins + d.word_off;
-    const unsigned long long t0 = st.ctl->t;
+    if ((L <= kWolffSmemMaxL) != SMEM) return;              // the other kernel takes this lattice
+    const uint32_t N = L * L;
+    const uint32_t n_words = N / 32;                         // packed words of the lattice
+    uint32_t* gwords = st.spins + d.word_off;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    WolffStore<SMEM> S;
+    S.L = L;
+    S.wn = wn;
+    if (SMEM) {
+        S.words = wolff_smem;
+        S.vis = wolff_smem + n_words;
+        S.q16 = reinterpret_cast<uint16_t*>(wolff_smem + 2 * n_words);
+        S.q32 = nullptr;
+        for (uint32_t i = tid; i < n_words; i += kWolffThreads) {
+            S.words[i] = gwords[i];
+            S.vis[i] = 0u;
+        }
+    } else {
+        S.words = gwords;
+        S.vis = sw.coins + d.site_off / 32;                 // zero between steps
+        S.q32 = sw.label + d.site_off;                       // up to L^2 sites
+        S.q16 = nullptr;
+    }
+    __syncthreads();
+    const unsigned long long t0 = st.ctl->t;
     for (long long step = 0; step < n_steps; ++step) {
         const uint32_t t = (uint32_t)(t0 + (unsigned long long)step);
         if (tid == 0) {
             const uint32_t r = philox(0u, t, d.sim, kPhaseWolffSeed, d.key0, d.key1).x;
             const uint32_t p0 = (uint32_t)(((uint64_t)r * N) >> 32);
-            s_b0 = site_bit(words, L, wn, p0 % L, p0 / L);
-            queue[0] = p0;
-            atomicOr(&vis[p0 >> 5], 1u << (p0 & 31u));
+            s_b0 = S.spin(p0 % L, p0 / L);
+            S.put(0, p0);
+            S.claim(p0);
             s_tail = 1;
         }
         __syncthreads();
         const uint32_t b0 = s_b0;
         uint32_t head = 0, tail = 1;
         // the growth, level by level
-        for (uint64_t level = 0; level < N && head < tail; ++level) {
+        for (uint32_t level = 0; level < N && head < tail; ++level) {
             for (uint32_t k = head + tid; k < tail; k += kWolffThreads) {
-                const uint32_t p = __ldcg(&queue[k]);
+                const uint32_t p = S.get(k);
                 const uint32_t y = p / L, x = p - y * L;
                 const uint32_t xr = (x + 1 == L) ? 0u : x + 1, xl = (x == 0) ? L - 1 : x - 1;
                 const uint32_t yd = (y + 1 == L) ? 0u : y + 1, yu = (y == 0) ? L - 1 : y - 1;
@@ -498,17 +549,15 @@ __global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, Sw
                 for (int n = 0; n < 4; ++n) {                // right, left, down, up
                     const uint32_t vx = n == 0 ? xr : (n == 1 ? xl : x), vy = n == 2 ? yd : (n == 3 ? yu : y);
                     const uint32_t v = vy * L + vx;
-                    if (site_bit(words, L, wn, vx, vy) != b0) continue;
-                    if (visited(vis, v)) continue;                           // already claimed (re-checked below)
+                    if (S.spin(vx, vy) != b0) continue;
+                    if (S.visited(v)) continue;              // already claimed (decided by claim below)
                     // the bond's owner: this site for right / down, the neighbour for left / up
                     const uint32_t owner = (n == 0 || n == 2) ? p : v, dir = (n < 2) ? 0u : 1u;
                     const uint4 r4 = philox(owner >> 1, t, d.sim, kPhaseWolffBond, d.key0, d.key1);
                     // lane 2 (owner & 1) + dir, by two-way selects
                     const uint32_t r = (owner & 1u) ? (dir ? r4.w : r4.z) : (dir ? r4.y : r4.x);
                     if (r >= d.thr) continue;
-                    const uint32_t bit = 1u << (v & 31u);
-                    if (atomicOr(&vis[v >> 5], bit) & bit) continue;
-                    queue[atomicAdd(&s_tail, 1u)] = v;
+                    if (S.claim(v)) S.put(atomicAdd(&s_tail, 1u), v);
                 }
             }
             __syncthreads();
@@ -519,16 +568,15 @@ __global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, Sw
         // energy change: 2 * sum over bonds leaving the cluster of sigma_0 sigma_v
         long long acc = 0;
         for (uint32_t k = tid; k < tail; k += kWolffThreads) {
-            const uint32_t p = __ldcg(&queue[k]);
+            const uint32_t p = S.get(k);
             const uint32_t y = p / L, x = p - y * L;
             const uint32_t xr = (x + 1 == L) ? 0u : x + 1, xl = (x == 0) ? L - 1 : x - 1;
             const uint32_t yd = (y + 1 == L) ? 0u : y + 1, yu = (y == 0) ? L - 1 : y - 1;
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
                 const uint32_t vx = n == 0 ? xr : (n == 1 ? xl : x), vy = n == 2 ? yd : (n == 3 ? yu : y);
-                const uint32_t v = vy * L + vx;
-                if (visited(vis, v)) continue;
-                acc += (site_bit(words, L, wn, vx, vy) == b0) ? 1 : -1;
+                if (S.visited(vy * L + vx)) continue;
+                acc += (S.spin(vx, vy) == b0) ? 1 : -1;
             }
         }
 #pragma unroll
@@ -537,11 +585,10 @@ __global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, Sw
         __syncthreads();
         // flips and visited bits cleared
         for (uint32_t k = tid; k < tail; k += kWolffThreads) {
-            const uint32_t p = __ldcg(&queue[k]);
+            const uint32_t p = S.get(k);
             const uint32_t y = p / L, x = p - y * L;
-            const uint32_t c = (x + y) & 1u, j = x >> 1;
-            atomicXor(&words[((size_t)c * L + y) * wn + (j >> 5)], 1u << (j & 31u));
-            atomicAnd(&vis[p >> 5], ~(1u << (p & 31u)));
+            S.flip(x, y);
+            S.unclaim(p);
         }
         if (tid == 0) {
             long long de = 0;
@@ -552,6 +599,8 @@ __global__ void __launch_bounds__(kWolffThreads, 1) wolff_kernel(DevState st, Sw
         }
         __syncthreads();
     }
+    if (SMEM)
+        for (uint32_t i = tid; i < n_words; i += kWolffThreads) gwords[i] = S.words[i];
 }
 
 }  // namespace
@@ -590,10 +639,24 @@ cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, cudaStream_t stream) {
+cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, uint32_t max_small_L, bool any_large,
+                         cudaStream_t stream) {
     if (sw.n <= 0 || n_steps <= 0) return cudaSuccess;
-    wolff_kernel<<<sw.n, kWolffThreads, 0, stream>>>(st, sw, (long long)n_steps);
-    return cudaGetLastError();
+    if (max_small_L > 0) {     // lattices with L <= kWolffSmemMaxL, in shared memory
+        const size_t smem = (size_t)max_small_L * max_small_L / 32 * 2 * 4 + (size_t)max_small_L * max_small_L * 2;
+        cudaError_t e = cudaFuncSetAttribute(wolff_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        wolff_kernel<true><<<sw.n, kWolffThreads, smem, stream>>>(st, sw, (long long)n_steps);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (any_large) {           // the others, with the queue and visited bits in the scratch
+        wolff_kernel<false><<<sw.n, kWolffThreads, 0, stream>>>(st, sw, (long long)n_steps);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
+
+uint32_t wolff_smem_max_L() { return kWolffSmemMaxL; }
 
 }  // namespace ising

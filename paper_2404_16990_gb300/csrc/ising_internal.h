@@ -179,7 +179,11 @@ cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream)
 cudaError_t launch_sw_compress(const SwState& sw, cudaStream_t stream);   // labels -> final roots
 // Wolff single-cluster steps of every lattice (ising_cluster.cu); the scratch
 // of the cluster step serves as queue (labels) and visited bits (coins).
-cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, cudaStream_t stream);
+// Lattices with L <= wolff_smem_max_L() run in shared memory (max_small_L =
+// the largest of them, 0 if none); any_large: some lattice is larger.
+cudaError_t launch_wolff(const DevState& st, const SwState& sw, int64_t n_steps, uint32_t max_small_L, bool any_large,
+                         cudaStream_t stream);
+uint32_t wolff_smem_max_L();
 
 int resident_occupancy(int threads, size_t smem_bytes);
 int stream_occupancy(int words_per_thread, int threads);
