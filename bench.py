@@ -146,6 +146,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def workload_sweeps(args) -> int:
+    return args.sweeps or (1000 if args.workload == "l16384" else 10000)
+
+
+def workload_config(args, rank: int = 0) -> dict:
+    """The `config` block both arms print for the workload: what is swept,
+    its sizes and the flip attempts of one step on one GPU."""
+    n_sw = workload_sweeps(args)
+    if args.workload == "l16384":
+        L = args.L
+        return {"workload": f"six {L}x{L} periodic lattices, T in {{1.5, 2.269185, 3.0}} x "
+                            f"{{cold, random seed 2}}, {n_sw} checkerboard sweeps per step, "
+                            f"E/M recorded every sweep",
+                "lattices_per_gpu": 6, "L": L, "sweeps_per_step": n_sw,
+                "flips_per_step_per_gpu": 6 * L * L * n_sw,
+                "l2": f"flushed between timed steps; working set {6 * L * L // 8 / 2**20:g} MiB "
+                      f"({'>' if 6 * L * L // 8 > 129e6 else '<'} 129 MB L2)"}
+    from paper_2404_16990_gb300 import workloads
+    wl = workloads.batch754(master_seed=20240426 + rank)
+    sites = sum(L * L for L in wl.Ls)
+    return {"workload": f"754 lattices, L in {{128,256,512,1024}} log-uniform, T ~ U[1.8,2.8], "
+                        f"random starts, {n_sw} sweeps per step, one persistent launch per step",
+            "lattices_per_gpu": 754, "spins_per_gpu": sites, "sweeps_per_step": n_sw,
+            "flips_per_step_per_gpu": sites * n_sw, "l2": "flushed between timed steps"}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline object)
 # ---------------------------------------------------------------------------
@@ -170,28 +196,53 @@ def time_oracle(L: int, seconds: float, max_sweeps: int | None = None):
             "seconds": t_total}
 
 
+def time_oracle_batch754(rank: int = 0):
+    """One sweep of every lattice of the 754-lattice workload by the oracle,
+    lattices spread over the host threads."""
+    import oracle
+    from paper_2404_16990_gb300 import workloads
+    cores = os.cpu_count() or 1
+    wl = workloads.batch754(master_seed=20240426 + rank)
+    sig = [oracle.init(L, sd, i) for i, (L, sd) in enumerate(zip(wl.Ls, wl.seeds))]
+    t0 = time.perf_counter()
+    oracle.sweeps_batch(sig, wl.temps, wl.seeds, list(range(len(sig))), 0, 1, n_threads=cores)
+    secs = time.perf_counter() - t0
+    flips = sum(L * L for L in wl.Ls)
+    return {"value": flips / (secs * 1e9), "unit": "flip/ns", "cores": cores, "kind": "oracle",
+            "sample": "1 sweep of all 754 lattices (random starts), oracle on "
+                      f"{cores} host threads (one lattice per thread at a time)",
+            "seconds": secs, "flips": flips}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     per_step = []
     for i in range(args.warmup + args.steps):
-        r = time_oracle(args.L, 0.0, max_sweeps=1)
+        if args.workload == "l16384":
+            r = time_oracle(args.L, 0.0, max_sweeps=1)
+            r["flips"] = args.L * args.L
+        else:
+            r = time_oracle_batch754()
         if i >= args.warmup:
             per_step.append(r)
     secs = sum(r["seconds"] for r in per_step)
-    flips = len(per_step) * args.L * args.L
-    value = flips / (secs * 1e9)
+    value = sum(r["flips"] for r in per_step) / (secs * 1e9)
     cb = dict(per_step[0])
     cb["value"] = value
-    cb["sample"] = f"each step: 1 sweep of one {args.L}x{args.L} lattice by the CPU oracle on {cb['cores']} threads"
+    if args.workload == "l16384":
+        cb["sample"] = (f"each step: 1 sweep of one {args.L}x{args.L} lattice (random start seed 2, "
+                        f"T=2.269185) by the CPU oracle on {cb['cores']} threads")
+    else:
+        cb["sample"] = "each step: " + cb["sample"]
     cb.pop("seconds", None)
+    cb.pop("flips", None)
     line = {"impl": "reference", "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs / len(per_step) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": f"{args.L}x{args.L} periodic lattice, checkerboard Metropolis, "
-                                   f"T=2.269185 random start (bounded sample of the six-run workload)"},
+            "config": workload_config(args),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "flip/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -215,7 +266,7 @@ def ours(args):
     sims = []
     tuned = None
     if args.workload == "l16384":
-        n_sw = args.sweeps or 1000
+        n_sw = workload_sweeps(args)
         seed = 2 + 1000 * rank  # independent replicas per rank; rank 0 is the configured seed 2
         with torch.cuda.stream(stream):
             for cold in (True, False):
@@ -224,7 +275,7 @@ def ours(args):
                 sims.append(s)
     else:
         from paper_2404_16990_gb300 import workloads
-        n_sw = args.sweeps or 10000
+        n_sw = workload_sweeps(args)
         wl = workloads.batch754(master_seed=20240426 + rank)
         with torch.cuda.stream(stream):
             s = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=0, stream=stream, device=dev)
@@ -332,20 +383,12 @@ def ours(args):
         cpu.pop("seconds", None)
 
     if rank == 0:
+        cfg = workload_config(args, rank)
+        assert cfg["flips_per_step_per_gpu"] == flips_per_step
         if args.workload == "l16384":
-            cfg = {"workload": f"six {L}x{L} periodic lattices, T in {{1.5, 2.269185, 3.0}} x "
-                               f"{{cold, random seed 2}}, {n_sw} checkerboard sweeps per step, "
-                               f"E/M recorded every sweep",
-                   "lattices_per_gpu": 6, "L": L, "sweeps_per_step": n_sw,
-                   "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps; "
-                   "working set 192 MiB > 129 MB L2", "kernel": "streaming half-sweep, CUDA graph",
-                   "plan": plan}
+            cfg.update({"kernel": "streaming half-sweep, CUDA graph", "plan": plan})
         else:
-            cfg = {"workload": f"754 lattices, L in {{128,256,512,1024}} log-uniform, T ~ U[1.8,2.8], "
-                               f"random starts, {n_sw} sweeps per step, one persistent launch per step",
-                   "lattices_per_gpu": 754, "spins_per_gpu": sites, "sweeps_per_step": n_sw,
-                   "flips_per_step_per_gpu": flips_per_step, "l2": "flushed between timed steps",
-                   "kernel": kname + ", CUDA graph", "plan": plan, "autotune_probe_flip_per_ns": tuned}
+            cfg.update({"kernel": kname + ", CUDA graph", "plan": plan, "autotune_probe_flip_per_ns": tuned})
         line = {
             "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

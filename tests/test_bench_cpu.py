@@ -1,0 +1,42 @@
+"""bench.py's reference arm on CPU: it times the oracle on a bounded sample
+and prints the contract's JSON line with the same workload `config` as the
+GPU arm."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*argv):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *argv], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT, check=True).stdout.strip().splitlines()
+    assert len(out) == 1
+    return json.loads(out[0])
+
+
+def test_reference_line_keys_and_config():
+    import argparse
+    import bench
+    line = _run("--impl", "reference", "--L", "512", "--steps", "2", "--warmup", "1")
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["metric"] == "spin-flip attempts/ns" and line["unit"] == "flip/ns" and line["higher_is_better"]
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    want = bench.workload_config(argparse.Namespace(workload="l16384", L=512, sweeps=0))
+    assert line["config"] == want
+    assert want["flips_per_step_per_gpu"] == 6 * 512 * 512 * 1000
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "flip/ns", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_batch_workload_config():
+    import argparse
+    import bench
+    cfg = bench.workload_config(argparse.Namespace(workload="batch754", L=16384, sweeps=0))
+    assert cfg["lattices_per_gpu"] == 754 and cfg["sweeps_per_step"] == 10000
+    assert cfg["flips_per_step_per_gpu"] == cfg["spins_per_gpu"] * 10000
