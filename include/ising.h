@@ -283,8 +283,9 @@ int ising_snapshot(ising_t h, void* dev_dst, size_t bytes);
  * avoids every other interior, so all patches move at once.  Each patch
  * proposes x' ~ q(. | ring), accepted iff log u < log alpha with
  * log alpha = -dE/T + log q(x) - log q(x') in FP64 (dE over the bonds touching
- * the interior) and u = ((r0 >> 5) 2^26 + (r1 >> 6) + 0.5) / 2^53 from lanes
- * 0, 1 of Philox counter (j, round, s, 5).  E and M are updated exactly.
+ * the interior) and u = ((r0 >> 5) 2^26 + (r1 >> 6) + 0.5) / 2^53 (FP64
+ * arithmetic: in (0, 1], 1.0 only for the top code) from lanes 0, 1 of
+ * Philox counter (j, round, s, 5).  E and M are updated exactly.
  * ------------------------------------------------------------------------ */
 #define ISING_NET_PARAMS 2945
 typedef struct ising_net* ising_net_t;

@@ -283,7 +283,10 @@ def u32_to_unit(r):
 
 
 def u53(r0, r1):
-    """53-bit uniform in (0, 1) from two u32 words: ((r0 >> 5) * 2^26 + (r1 >> 6) + 0.5) / 2^53."""
+    """53-bit uniform from two u32 words: ((r0 >> 5) * 2^26 + (r1 >> 6) + 0.5) / 2^53
+    in float64 arithmetic, i.e. (k + 1/2) / 2^53 rounded to nearest-even for
+    the code k.  It lies in (0, 1]: for k >= 2^52 the half rounds, and the top
+    code (probability 2^-53) gives exactly 1.0."""
     return (float((int(r0) >> 5) * 67108864 + (int(r1) >> 6)) + 0.5) / 9007199254740992.0
 
 

@@ -178,3 +178,79 @@ def test_fp8_forward_is_close_to_bf16_and_keeps_the_mask():
     order = np.arange(100).reshape(10, 10)
     before = order <= order[4, 4]
     assert np.array_equal(z8[:, before], z8b[:, before])
+
+
+def _forced_draws(target, P):
+    """u32 draws that make a sampler obeying x_p = +1 iff R_p < thr_p
+    produce `target`'s interior (0 is below every positive threshold,
+    2^32 - 1 below none)."""
+    x = np.asarray(target, np.int64)[:, 1:P + 1, 1:P + 1].reshape(len(target), P * P)
+    return np.where(x > 0, 0.0, 4294967295.0)
+
+
+@pytest.mark.parametrize("S,gain", [(4, 2.0), (10, 0.7)])
+def test_sampler_path_probability_is_q(S, gain):
+    # the probability with which the sampler produces x, the product of its
+    # per-site thresholds / 2^32 along x's path, equals q(x | ring) up to the
+    # 2^-32 quantization and the float32 sigmoid
+    P = S - 2
+    flat = ol.init_params(31, gain=gain)
+    target = rand_windows(64, S, 17)
+    got, lq, thr = ol.sample(target, flat, _forced_draws(target, P))
+    assert np.array_equal(got, target)
+    x = target[:, 1:P + 1, 1:P + 1].reshape(64, P * P)
+    p_plus = thr / 4294967296.0
+    log_path = np.where(x > 0, np.log(p_plus), np.log1p(-p_plus)).sum(axis=1)
+    z, _ = ol.forward(target, flat)
+    assert np.allclose(lq, ol.log_q(target, z), atol=0, rtol=0)
+    assert np.max(np.abs(log_path - lq)) < 2e-5 * P * P
+
+
+def test_sampler_distribution_matches_q():
+    # independent uniform u32 draws: chi^2 of the 16 interiors of a 2x2 patch
+    # against q(. | ring), two rings sampled in one batch
+    from scipy import stats
+    flat = ol.init_params(41, gain=2.0)
+    rng = np.random.default_rng(43)
+    n, rings = 6000, rand_windows(2, 4, 47)
+    R = rng.integers(0, 2**32, size=(2 * n, 4)).astype(np.float64)
+    got, _, _ = ol.sample(np.repeat(rings, n, axis=0), flat, R)
+    codes = ((got[:, 1:3, 1:3].reshape(2 * n, 4) > 0) * (1 << np.arange(4))).sum(axis=1)
+    all16 = np.where((np.arange(16)[:, None] >> np.arange(4)) & 1, 1, -1).reshape(16, 2, 2)
+    for b in range(2):
+        counts = np.bincount(codes[b * n:(b + 1) * n], minlength=16)
+        w = np.repeat(rings[b][None], 16, axis=0)
+        w[:, 1:3, 1:3] = all16
+        z, _ = ol.forward(w, flat)
+        expct = np.exp(ol.log_q(w, z)) * n
+        o, e, acc_o, acc_e = [], [], 0.0, 0.0         # rarest first, pooled to >= 10 expected
+        for i in np.argsort(expct):
+            acc_o += counts[i]
+            acc_e += expct[i]
+            if acc_e >= 10:
+                o.append(acc_o)
+                e.append(acc_e)
+                acc_o = acc_e = 0.0
+        o[-1] += acc_o
+        e[-1] += acc_e
+        o, e = np.array(o), np.array(e)
+        chi2 = ((o - e) ** 2 / e).sum()
+        assert len(o) >= 4 and stats.chi2.sf(chi2, len(o) - 1) > 1e-4, (b, chi2, len(o))
+
+
+def test_u53_is_the_rounded_half_code_and_uniform():
+    # u53 = (k + 1/2) / 2^53, k = (r0 >> 5) 2^26 + (r1 >> 6), correctly rounded
+    # to float64 (exact rational arithmetic here); so u is in (0, 1] and only
+    # the top code reaches 1.0
+    from fractions import Fraction
+    from scipy import stats
+    rng = np.random.default_rng(5)
+    words = [(0, 0), (0, 63), (0, 64), (31, 2**32 - 1), (32, 0), (2**31, 0), (2**32 - 1, 2**32 - 65),
+             (2**32 - 1, 2**32 - 1)] + [tuple(int(v) for v in w) for w in rng.integers(0, 2**32, size=(2000, 2))]
+    for r0, r1 in words:
+        k = (r0 >> 5) * 2**26 + (r1 >> 6)
+        assert ol.u53(r0, r1) == float(Fraction(2 * k + 1, 2**54)), (r0, r1)
+    assert ol.u53(0, 0) == 2.0**-54 and ol.u53(0, 64) - ol.u53(0, 0) == 2.0**-53
+    assert ol.u53(2**32 - 1, 2**32 - 65) < 1.0 == ol.u53(2**32 - 1, 2**32 - 1)
+    u = [ol.u53(int(a), int(b)) for a, b in rng.integers(0, 2**32, size=(20000, 2))]
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
