@@ -30,6 +30,10 @@ def test_tau_int_ar1_closed_form(rho):
     exact = (1 + rho) / (2 * (1 - rho))
     bias = rho ** (W + 1) / (1 - rho) if rho > 0 else 0.0   # truncated tail
     assert abs(tau - exact) < 4 * err + bias + 1e-3, (tau, exact, err, W)
+    # the window stops at the first lag with W >= c tau(W); the step from
+    # tau(W-1) to tau(W) is rho(W), so 0 <= W - c tau < 1 - c rho(W), and
+    # rho(W) is tiny at these windows
+    assert 0.0 <= W - 6.0 * tau < 1.5, (W, tau)
 
 
 def test_tau_int_constant_and_alternating():
