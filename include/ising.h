@@ -229,7 +229,8 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int sweeps_per_unit, int threads);
 
 /* Autotuner: time candidate plans (resident with sweeps_per_unit in {8, 32,
- * 128} and block sizes {auto, 256, 512} when some lattice has L <= 1024;
+ * 128} and block sizes {auto, 256, 512} when some lattice has L <= 1024 --
+ * RESIDENT if every lattice has, else MIXED;
  * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {1, 2, 4, 8},
  * threads in {128, 256}, and the persistent streaming kernel with the same
  * tilings) for probe_sweeps sweeps each on the handle's stream
@@ -458,7 +459,7 @@ int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes
  * Metropolis sweeps share the counter and may be mixed. */
 int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes);
 
-/* Cluster labels of lattice `sim` for the step the handle would take next/* Cluster labels of lattice `sim` for the step the handle would take next
+/* Cluster labels of lattice `sim` for the step the handle would take next
  * (its current sweep counter), without taking it: host_labels[L*L]
  * (caller-owned) receives, for every site p = y*L + x, the smallest site
  * index of its cluster.  Synchronises the stream.  The spins and the sweep

@@ -882,9 +882,9 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
         int rc = apply_cand(h, cached);
         if (rc == ISING_OK) return ISING_OK;
     }
-    // candidates: the resident kernel (when every lattice has L <= 1024) with
-    // several unit sizes and block sizes, and the streaming and persistent
-    // kernels with several tilings
+    // candidates: the resident kernel with several unit sizes and block sizes
+    // when some lattice has L <= 1024 (RESIDENT if all do, else MIXED), and
+    // the streaming and persistent kernels with several tilings
     std::vector<TuneCand> cands;
     bool all_small = true, any_small = false;
     for (int L : h->L) {
@@ -912,8 +912,7 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     std::vector<char> saved(nbytes);
     rc = ising_save(h, saved.data(), nbytes);
     if (rc != ISING_OK) return rc;
-    const Plan plan0 = h->plan;
-    const bool graph0 = h->graph;   // candidates are timed the way sweeps will run (graph replay or not)
+    const Plan plan0 = h->plan;   // candidates are timed the way sweeps will run (graph replay or not)
     double sites = 0;
     for (int L : h->L) sites += (double)L * L;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -937,7 +936,6 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    (void)graph0;
     if (best < 0) {
         h->plan = plan0;
         build_tables(h);
