@@ -36,6 +36,17 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+@pytest.mark.parametrize("lang,compiler,std", [("c", "gcc", "-std=c99"), ("c++", "g++", "-std=c++17")])
+def test_headers_compile_cleanly_as_c_and_cxx(lang, compiler, std, tmp_path):
+    # a plain C ABI: every header compiles alone, warning-free, in C and C++
+    for hdr in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = tmp_path / ("use." + ("c" if lang == "c" else "cpp"))
+        src.write_text(f'#include "{os.path.basename(hdr)}"\nint main(void) {{ return 0; }}\n')
+        r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                            "-I" + os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, (hdr, r.stderr)
+
+
 def test_library_exports_every_declared_symbol():
     lib_path = ising._build.build()
     lib = ctypes.CDLL(lib_path)
