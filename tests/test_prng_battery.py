@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import itertools
 import math
+import zlib
 
 import numpy as np
 import pytest
@@ -135,3 +136,38 @@ def test_library_battery_matches_oracle():
             assert abs(p_lib[j] - p_ref[j]) <= 1e-9 + 1e-7 * p_ref[j], (name, len(w), p_lib[j], p_ref[j])
     with pytest.raises(ising.IsingError):
         ising.ising_prng_battery(np.zeros(4095, dtype=np.uint32))
+
+
+def test_statistics_by_hand():
+    # the statistic each test returns, counted by hand on short strings
+    for s, V in (("1100", 2), ("1010", 4), ("0110100111", 6), ("0000011111", 2)):
+        b = [int(ch) for ch in s]
+        assert pb.runs(b)[1] == V, s                      # number of maximal blocks of equal bits
+    # block frequency, M = 4 on 11110000 0110: blocks 1111, 0000, 0110 have
+    # 4, 0, 2 ones: 4M sum (ones/M - 1/2)^2 = 16 (1/4 + 1/4 + 0) = 8
+    assert pb.block_frequency([1, 1, 1, 1, 0, 0, 0, 0, 0, 1, 1, 0], M=4)[1] == 8.0
+    # longest run of ones per 8-bit block, classes <= 1, 2, 3, >= 4 (lo = 1, hi = 4):
+    # 01101110 -> 3, 00000000 -> 0, 11111011 -> 5, 10101010 -> 1 ; counts 2, 0, 1, 1
+    blocks = "01101110" "00000000" "11111011" "10101010"
+    p8 = pb.longest_run_class_probs(8, 1, 4)
+    e = 4 * p8
+    want = float((((np.array([2, 0, 1, 1]) - e) ** 2) / e).sum())
+    assert abs(pb.longest_run([int(ch) for ch in blocks], M=8, lo=1, hi=4)[1] - want) < 1e-12
+    # float uniformity with 4 bins on 0.1, 0.3, 0.35, 0.9: counts 1, 2, 0, 1 against 1 each
+    assert pb.float_uniformity([0.1, 0.3, 0.35, 0.9], bins=4)[1] == 2.0
+    # float pairs with 2 bins: (0.1, 0.2), (0.6, 0.7), (0.1, 0.9), (0.2, 0.3): cells 00 x2, 11, 01
+    assert pb.float_pairs([0.1, 0.2, 0.6, 0.7, 0.1, 0.9, 0.2, 0.3], bins=2)[1] == 2.0
+
+
+@pytest.mark.parametrize("name,words", [("block_frequency", 512), ("longest_run", 512),
+                                        ("float_uniformity", 1000), ("float_pairs", 2000)])
+def test_chi2_pvalues_uniform_at_scale(name, words):
+    # under fair input every p-value is uniform; thousands of short streams
+    # resolve the degrees of freedom and normalisation of each chi^2 test
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    fn = getattr(pb, name)
+    P = []
+    for _ in range(4000):
+        w = rng.integers(0, 2**32, size=words, dtype=np.uint64).astype(np.uint32)
+        P.append(fn(pb.floats(w) if name.startswith("float") else pb.bits(w))[0])
+    assert stats.kstest(P, "uniform").pvalue > 1e-3, name
