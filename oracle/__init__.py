@@ -62,8 +62,6 @@ def _load():
         lib.oracle_site_random.restype = ctypes.c_uint32
         lib.oracle_thresholds.argtypes = [ctypes.c_double, u32p]
         lib.oracle_thresholds.restype = ctypes.c_int
-        lib.oracle_init.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i8p]
-        lib.oracle_init.restype = ctypes.c_int
         lib.oracle_init_parallel.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                              ctypes.c_int, i8p, ctypes.c_int]
         lib.oracle_init_parallel.restype = ctypes.c_int

@@ -99,24 +99,6 @@ int oracle_thresholds(double T, uint32_t thr[2])
 
 static inline int wrap(int i, int L) { return ((i % L) + L) % L; }
 
-/* Initial state: mode 1 = cold (all +1); mode 0 = random, sigma = +1 iff the
- * top bit of the site's draw (phase 2, sweep 0, p = y*L + x) is 0. */
-int oracle_init(int L, uint64_t seed, uint32_t s, int mode, int8_t* sigma)
-{
-    if (L < 2 || (L & 1)) return -1;
-    for (int y = 0; y < L; ++y)
-        for (int x = 0; x < L; ++x) {
-            int8_t v = 1;
-            if (mode == 0) {
-                uint32_t p = (uint32_t)y * (uint32_t)L + (uint32_t)x;
-                uint32_t r = oracle_site_random(seed, p, 0u, s, 2u);
-                v = (r >> 31) ? (int8_t)-1 : (int8_t)1;
-            }
-            sigma[(size_t)y * L + x] = v;
-        }
-    return 0;
-}
-
 /* H = -sum over every site of sigma * (right + down neighbour): each bond
  * once. */
 int64_t oracle_energy(int L, const int8_t* sigma)
@@ -261,7 +243,9 @@ void oracle_window_sweeps(int L, int8_t* win, int y0, int x0, int h, int w,
     }
 }
 
-/* Full-lattice initial state split over rows (same per-site definition). */
+/* Initial state: mode 1 = cold (all +1); mode 0 = random, sigma = +1 iff the
+ * top bit of the site's draw (phase 2, sweep 0, p = y*L + x) is 0.  Rows may
+ * be split across threads: every site has its own draw. */
 int oracle_init_parallel(int L, uint64_t seed, uint32_t s, int mode, int8_t* sigma, int n_threads)
 {
     if (L < 2 || (L & 1)) return -1;

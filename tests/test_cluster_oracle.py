@@ -234,3 +234,21 @@ def test_sw_beats_metropolis_autocorrelation_at_tc():
     tau_mp = ostats.tau_int(np.abs(M_mp))[0]
     assert tau_sw < 10.0, tau_sw
     assert tau_mp > 5 * tau_sw, (tau_mp, tau_sw)
+
+
+@pytest.mark.parametrize("L,T", [(8, 2.0), (16, exact.T_C), (32, 3.0)])
+def test_sw_step_flips_each_cluster_by_its_root_coin(L, T):
+    # one step = this step's bonds -> clusters named by their smallest site r0
+    # -> every site flips iff the top bit of the phase-8 draw of r0 (lane r0 & 3
+    # of Philox block (r0 >> 2, t, s, 8)) is 1
+    seed, s = 0x5151, 3
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    sigma = oracle.init(L, seed, s)
+    for t in range(3):
+        before = sigma.copy()
+        lab, _ = oracle.sw_labels(oracle.sw_bonds(before, T, seed, s, t))
+        oracle.sw_sweeps(sigma, T, seed, s, t, 1)
+        coin = {int(r): int(oracle.philox4x32_10([int(r) >> 2, t, s, 8], key)[int(r) & 3]) >> 31
+                for r in np.unique(lab)}
+        want = np.where(np.vectorize(coin.get)(lab) == 1, -before, before)
+        assert np.array_equal(sigma, want), (L, T, t)

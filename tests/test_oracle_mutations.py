@@ -1,7 +1,9 @@
 """Plant plausible mistakes in a copy of the oracle source (on the CPU) and
-check that at least one pin catches each: a dropped neighbour, swapped
-thresholds, the colour order reversed, zero-energy moves rejected, a wrong
-Philox multiplier, an energy sign error."""
+check that at least one pin catches each: a dropped or wrong neighbour,
+swapped, ceiled or mis-scaled thresholds, the colour order or colour rule,
+zero-energy moves rejected, the sign of dE, Philox's multiplier, key
+schedule, rounds and word order, the output lane, the energy's sign or a
+dropped bond, the sense of the initial-state bit."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,6 +26,21 @@ MUTATIONS = {
                             "        flip = 0;\n    } else {\n        uint32_t p"),
     "philox_multiplier": ("#define ORC_PHILOX_MUL_A 0xD2511F53u", "#define ORC_PHILOX_MUL_A 0xD2511F55u"),
     "energy_sign": ("e -= (int64_t)(s * (r + d));", "e += (int64_t)(s * (r + d));"),
+    "energy_down_bond_dropped": ("e -= (int64_t)(s * (r + d));", "e -= (int64_t)(s * r);"),
+    "philox_key_bumped_before_first_round": ("        if (round > 0) {\n            k0 += ORC_PHILOX_WEYL_A;",
+                                             "        if (round >= 0) {\n            k0 += ORC_PHILOX_WEYL_A;"),
+    "philox_low_words_swapped": ("uint32_t n1 = (uint32_t)prod_b;", "uint32_t n1 = (uint32_t)prod_a;"),
+    "philox_seven_rounds": ("for (int round = 0; round < 10; ++round)", "for (int round = 0; round < 7; ++round)"),
+    "output_lane_from_wrong_bits": ("return out[p & 3u];", "return out[(p >> 1) & 3u];"),
+    "threshold_ceil": ("(uint32_t)floor(v);", "(uint32_t)ceil(v);"),
+    "threshold_energy_scale": ("double dE = 4.0 * (double)(k + 1);", "double dE = 2.0 * (double)(k + 1);"),
+    "up_neighbour_is_the_site": ("int h = sigma[(size_t)wrap(y - 1, L) * L + x]", "int h = sigma[(size_t)wrap(y, L) * L + x]"),
+    "column_colouring": ("if (((x + y) & 1) == c) update_site", "if ((x & 1) == c) update_site"),
+    "dE_sign": ("int dE = 2 * sigma[i] * h;", "int dE = -2 * sigma[i] * h;"),
+    "initial_bit_sense": ("                v = (oracle_site_random(seed, p, 0u, s, 2u) >> 31) ? (int8_t)-1 : (int8_t)1;\n"
+                          "            }\n            sigma[(size_t)y * L + x] = v;",
+                          "                v = (oracle_site_random(seed, p, 0u, s, 2u) >> 31) ? (int8_t)1 : (int8_t)-1;\n"
+                          "            }\n            sigma[(size_t)y * L + x] = v;"),
 }
 
 
@@ -32,6 +49,9 @@ def _caught(variant_so) -> list:
     with oracle.use_library(variant_so):
         checks = [
             ("kat", lambda: [pins.test_philox_known_answers(c, k, e) for c, k, e in pins._kat_rows()]),
+            ("keying", lambda: pins.test_site_random_keying()),
+            ("thresholds", lambda: (pins.test_thresholds_exact(), pins.test_thresholds_limits_and_errors())),
+            ("init", lambda: pins.test_init_cold_and_random()),
             ("t0_golden", lambda: [pins.test_zero_temperature_worked_cases(*c) for c in pins._golden_t0_cases()]),
             ("closed_forms", lambda: pins.test_energy_closed_forms(4)),
             ("chi2_4x4", lambda: pins.test_4x4_joint_distribution_matches_enumeration(exact.T_C)),
@@ -74,6 +94,16 @@ SW_MUTATIONS = {
     "sw_left_neighbour_missed": ("if (bonds[left] & 1u) nb[k++] = left;", ""),
     "sw_same_lane_both_bonds": ("uint32_t r_down = out[2u * (p & 1u) + 1u];",
                                 "uint32_t r_down = out[2u * (p & 1u)];"),
+    "sw_threshold_ceil": ("*thr = (v >= 4294967296.0) ? 0xFFFFFFFFu : (uint32_t)floor(v);",
+                          "*thr = (v >= 4294967296.0) ? 0xFFFFFFFFu : (uint32_t)ceil(v);"),
+    "sw_right_neighbour_not_wrapped": ("int8_t right = sigma[(size_t)y * L + (x + 1) % L];",
+                                       "int8_t right = sigma[(size_t)y * L + (x + 1 < L ? x + 1 : x)];"),
+    "sw_up_neighbour_missed": ("if (bonds[up] & 2u) nb[k++] = up;", ""),
+    "sw_label_is_the_discoverer": ("label[nb[i]] = (uint32_t)start;", "label[nb[i]] = u;"),
+    "sw_every_cluster_flipped": ("if (coin) sigma[p] = (int8_t)(-sigma[p]);", "sigma[p] = (int8_t)(-sigma[p]); (void)coin;"),
+    "sw_coin_from_the_bond_phase": ("#define ORC_SW_PHASE_COIN 8u", "#define ORC_SW_PHASE_COIN 7u"),
+    "sw_coin_low_bit": ("uint32_t coin = oracle_site_random(seed, root, t, s, ORC_SW_PHASE_COIN) >> 31;",
+                        "uint32_t coin = oracle_site_random(seed, root, t, s, ORC_SW_PHASE_COIN) & 1u;"),
 }
 
 
@@ -82,6 +112,7 @@ def _caught_sw(variant_so) -> list:
     with oracle.use_library(variant_so):
         checks = [
             ("threshold", swpins.test_sw_threshold_exact),
+            ("root_coin", lambda: swpins.test_sw_step_flips_each_cluster_by_its_root_coin(16, exact.T_C)),
             ("bonds", lambda: swpins.test_bonds_between_equal_spins_at_rate_p(exact.T_C)),
             ("lanes", swpins.test_bonds_right_and_down_draws_are_distinct_lanes),
             ("labels", lambda: swpins.test_labels_match_connected_components(16, 0.45)),
@@ -122,6 +153,15 @@ MUTATIONS_3D = {
     "3d_colour_rule": ("if (((x + y + z) & 1) != c) continue;", "if (((x + y) & 1) != c) continue;"),
     "3d_energy_missing_axis": ("sigma[at3(L, x + 1, y, z)] + sigma[at3(L, x, y + 1, z)] + sigma[at3(L, x, y, z + 1)];",
                                "sigma[at3(L, x + 1, y, z)] + sigma[at3(L, x, y + 1, z)];"),
+    "3d_threshold_ceil": ("thr[k] = (v >= 4294967296.0) ? 0xFFFFFFFFu : (uint32_t)floor(v);",
+                          "thr[k] = (v >= 4294967296.0) ? 0xFFFFFFFFu : (uint32_t)ceil(v);"),
+    "3d_threshold_scale": ("double v = ldexp(exp(-4.0 * (double)(k + 1) / T), 32);",
+                           "double v = ldexp(exp(-2.0 * (double)(k + 1) / T), 32);"),
+    "3d_dE_sign": ("int dE = 2 * sigma[i] * h;", "int dE = -2 * sigma[i] * h;"),
+    "3d_white_first": ("        half_sweep3(L, sigma, 0, thr, seed, s, t);\n        half_sweep3(L, sigma, 1, thr, seed, s, t);",
+                       "        half_sweep3(L, sigma, 1, thr, seed, s, t);\n        half_sweep3(L, sigma, 0, thr, seed, s, t);"),
+    "3d_y_neighbour_twice": ("sigma[at3(L, x, y - 1, z)] +\n                        sigma[at3(L, x, y + 1, z)]",
+                             "sigma[at3(L, x, y + 1, z)] +\n                        sigma[at3(L, x, y + 1, z)]"),
 }
 
 
@@ -129,6 +169,7 @@ def _caught_3d(variant_so) -> list:
     caught = []
     with oracle.use_library(variant_so):
         checks = [
+            ("thresholds", pins3d.test_thresholds3d_exact),
             ("closed_forms", lambda: pins3d.test_energy3d_closed_forms(4)),
             ("chi2_2x2x2", lambda: pins3d.test_2x2x2_joint_distribution_matches_enumeration(4.5)),
             ("chi2_2x2x2_cold", lambda: pins3d.test_2x2x2_joint_distribution_matches_enumeration(2.0)),
@@ -171,6 +212,13 @@ WOLFF_MUTATIONS = {
     "wolff_same_lane_both_bonds": ("2u * (p & 1u) + (uint32_t)dir", "2u * (p & 1u)"),
     "wolff_seed_mapping": ("return (uint32_t)((r * (uint64_t)L * (uint64_t)L) >> 32);",
                            "return (uint32_t)(r % ((uint64_t)L * (uint64_t)L));"),
+    "wolff_only_the_seed_flipped": ("for (size_t i = 0; i < tail; ++i) sigma[queue[i]] = (int8_t)(-s0);",
+                                    "sigma[queue[0]] = (int8_t)(-s0);"),
+    "wolff_seed_from_another_lane": ("uint64_t r = wolff_draw(seed, 0u, t, s, ORC_WOLFF_PHASE_SEED, 0u);",
+                                     "uint64_t r = wolff_draw(seed, 0u, t, s, ORC_WOLFF_PHASE_SEED, 1u);"),
+    "wolff_bond_directions_swapped": ("const int dir[4] = { 0, 0, 1, 1 };", "const int dir[4] = { 1, 1, 0, 0 };"),
+    "wolff_down_neighbour_misplaced": ("const uint32_t down = (uint32_t)((y + 1) % L) * L + (uint32_t)x;",
+                                       "const uint32_t down = (uint32_t)((y + 1) % L) * L + (uint32_t)((x + 1) % L);"),
 }
 
 
