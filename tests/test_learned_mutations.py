@@ -3,7 +3,8 @@
 test_learned_oracle.py catches each: the sampler's comparison or sigmoid, the
 sign in log q, the Metropolis-Hastings ratio, the local energy, the two
 autoregressive masks, the backward pass, Adam's bias correction, the patch
-offsets, the 53-bit uniform and the bf16 / e4m3 rounding."""
+offsets, the round's acceptance test, the 53-bit uniform and the bf16 / e4m3
+rounding."""
 from __future__ import annotations
 
 import inspect
@@ -35,6 +36,8 @@ MUTATIONS = {
     "round_dm_sign": ("dMt += int(new[j][1:P + 1, 1:P + 1].astype(np.int64).sum() - wins[j]",
                       "dMt -= int(new[j][1:P + 1, 1:P + 1].astype(np.int64).sum() - wins[j]"),
     "u53_high_word_scale": ("(int(r0) >> 5) * 67108864", "(int(r0) >> 5) * 134217728"),
+    "round_acceptance_reversed": ("ok = math.log(u) < log_alpha", "ok = math.log(u) > log_alpha"),
+    "round_uniform_ignored": ("ok = math.log(u) < log_alpha", "ok = 0.0 < log_alpha"),
     "bf16_truncates": ("((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000)", "(u & 0xFFFF0000)"),
     "e4m3_three_exponent_bits": ("e = np.maximum(e, -6.0)", "e = np.maximum(e, -2.0)"),
 }
@@ -50,6 +53,7 @@ CHECKS = [
     ("sampler_path_4", lambda: pins.test_sampler_path_probability_is_q(4, 2.0)),
     ("sampler_path_10", lambda: pins.test_sampler_path_probability_is_q(10, 0.7)),
     ("round_bookkeeping", lambda: pins.test_learned_round_runs_and_keeps_energy_bookkeeping()),
+    ("round_limits", lambda: pins.test_learned_round_limits_with_a_uniform_proposal()),
     ("u53", lambda: pins.test_u53_is_the_rounded_half_code_and_uniform()),
     ("e4m3", lambda: pins.test_e4m3_rounding_matches_torch()),
     ("bf16", lambda: pins.test_bf16_rounding_matches_torch()),

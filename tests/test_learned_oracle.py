@@ -254,3 +254,22 @@ def test_u53_is_the_rounded_half_code_and_uniform():
     assert ol.u53(2**32 - 1, 2**32 - 65) < 1.0 == ol.u53(2**32 - 1, 2**32 - 1)
     u = [ol.u53(int(a), int(b)) for a, b in rng.integers(0, 2**32, size=(20000, 2))]
     assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+def test_learned_round_limits_with_a_uniform_proposal():
+    # all-zero parameters: z = 0, q uniform, so log alpha = -dE / T.  As
+    # T -> inf every proposal is accepted; as T -> 0 exactly those that do not
+    # raise the energy (Metropolis-Hastings in both limits)
+    L, seed = 32, 9
+    flat = np.zeros(ol.N_PARAMS)
+    for T, rnd in ((1e9, 0), (1e9, 1), (0.05, 2), (0.05, 3)):
+        s = oracle.init(L, seed, 0)
+        acc, _, _, recs = ol.learned_round(s, flat, T, seed, 0, rnd)
+        assert all(abs(r["lq_old"] - r["lq_new"]) < 1e-12 for r in recs)
+        for r in recs:
+            assert r["accept"] == (r["dE"] <= 0 if T < 1 else True), (T, r["dE"], r["log_alpha"])
+        assert acc == sum(r["accept"] for r in recs)
+        if T > 1:
+            assert acc == len(recs)
+        else:
+            assert any(r["dE"] > 0 for r in recs) and any(r["dE"] < 0 for r in recs)
