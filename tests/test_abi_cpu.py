@@ -47,6 +47,19 @@ def test_headers_compile_cleanly_as_c_and_cxx(lang, compiler, std, tmp_path):
         assert r.returncode == 0, (hdr, r.stderr)
 
 
+def test_plain_c_example_builds_against_the_library(tmp_path):
+    # paper_2404_16990_gb300/examples/sweep.c uses the ABI from C alone: it
+    # compiles warning-free and links against libising.so (not run: no GPU here)
+    lib_path = ising._build.build()
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    src = os.path.join(ROOT, "paper_2404_16990_gb300", "examples", "sweep.c")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", src, "-I" + os.path.join(ROOT, "include"),
+                        "-I" + os.path.join(cuda, "include"), "-L" + os.path.dirname(lib_path), "-lising",
+                        "-L" + os.path.join(cuda, "lib64"), "-lcudart", "-o", str(tmp_path / "sweep")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol():
     lib_path = ising._build.build()
     lib = ctypes.CDLL(lib_path)
