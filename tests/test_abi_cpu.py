@@ -60,6 +60,17 @@ def test_plain_c_example_builds_against_the_library(tmp_path):
     assert r.returncode == 0, r.stderr
 
 
+def test_c_example_recorded_output_is_the_oracles():
+    # the E/N and M/N that sweep.c's header records from a GB300 run equal the
+    # oracle's for the same lattice (256^2, seed 1, sim 0, T = 2.269185, 1000 sweeps)
+    import oracle
+    text = open(os.path.join(ROOT, "paper_2404_16990_gb300", "examples", "sweep.c")).read()
+    m = re.search(r"E/N = (-?[0-9.]+), M/N = (-?[0-9.]+)", text)
+    sigma = oracle.init(256, 1, 0)
+    E, M = oracle.sweeps(sigma, 2.269185, 1, 0, 0, 1000, n_threads=max(1, min(8, os.cpu_count() or 1)))
+    assert m and m.group(1) == f"{E[-1] / 65536:.6f}" and m.group(2) == f"{M[-1] / 65536:.6f}"
+
+
 def test_library_exports_every_declared_symbol():
     lib_path = ising._build.build()
     lib = ctypes.CDLL(lib_path)
