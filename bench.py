@@ -32,6 +32,7 @@ T_RUNS = (1.5, 2.269185, 3.0)
 # the accept decision (3), the bitsliced neighbour count (0.5)
 OPS_PER_SITE = 18.5
 SMS = 152
+SINGLE_THREAD_L = 4096   # lattice of the single-thread oracle figure
 INT_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
@@ -175,9 +176,22 @@ def workload_config(args, rank: int = 0) -> dict:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline object)
 # ---------------------------------------------------------------------------
-def time_oracle(L: int, seconds: float, max_sweeps: int | None = None):
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
+def time_oracle(L: int, seconds: float, max_sweeps: int | None = None, threads: int | None = None):
     import oracle
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     lat = oracle.init(L, 2, 0, n_threads=cores)
     done, t_total = 0, 0.0
     n = 1
@@ -191,9 +205,24 @@ def time_oracle(L: int, seconds: float, max_sweeps: int | None = None):
         n = min(n * 2, 64)
     flips = done * L * L
     return {"value": flips / (t_total * 1e9), "unit": "flip/ns", "cores": cores, "kind": "oracle",
-            "sample": f"{done} sweeps of one {L}x{L} lattice (random start seed 2, T=2.269185, E/M each "
-                      f"sweep), oracle on {cores} host threads (rows of one colour split across threads)",
+            "sample": f"{done} sweep{'s' if done != 1 else ''} of one {L}x{L} lattice (random start seed 2, "
+                      f"T=2.269185, E/M each sweep), oracle on "
+                      + ("1 host thread" if cores == 1 else
+                         f"{cores} host threads (rows of one colour split across threads)"),
             "seconds": t_total}
+
+
+def cpu_baseline(L: int, seconds: float) -> dict:
+    """The `cpu_baseline` object: the oracle on every host thread for about
+    `seconds` on one L x L lattice, plus a single-thread figure on a lattice of
+    at most 4096^2 (one 16384^2 sweep on one thread would take tens of
+    seconds) and the host CPU's model."""
+    cpu = time_oracle(L, seconds)
+    cpu.pop("seconds", None)
+    one = time_oracle(min(L, SINGLE_THREAD_L), seconds / 4, threads=1)
+    cpu["single_thread"] = {"value": one["value"], "unit": "flip/ns", "sample": one["sample"]}
+    cpu["cpu_model"] = host_cpu_model()
+    return cpu
 
 
 def time_oracle_batch754(rank: int = 0):
@@ -238,6 +267,7 @@ def reference_arm(args):
         cb["sample"] = "each step: " + cb["sample"]
     cb.pop("seconds", None)
     cb.pop("flips", None)
+    cb["cpu_model"] = host_cpu_model()
     line = {"impl": "reference", "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs / len(per_step) * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -379,8 +409,7 @@ def ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "l16384":
-        cpu = time_oracle(L, args.cpu_seconds)
-        cpu.pop("seconds", None)
+        cpu = cpu_baseline(L, args.cpu_seconds)
 
     if rank == 0:
         cfg = workload_config(args, rank)

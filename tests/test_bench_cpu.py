@@ -30,6 +30,7 @@ def test_reference_line_keys_and_config():
     assert want["flips_per_step_per_gpu"] == 6 * 512 * 512 * 1000
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert cb["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": "flip/ns", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
@@ -40,3 +41,22 @@ def test_batch_workload_config():
     cfg = bench.workload_config(argparse.Namespace(workload="batch754", L=16384, sweeps=0))
     assert cfg["lattices_per_gpu"] == 754 and cfg["sweeps_per_step"] == 10000
     assert cfg["flips_per_step_per_gpu"] == cfg["spins_per_gpu"] * 10000
+
+
+def test_oracle_timing_on_one_thread():
+    import bench
+    r = bench.time_oracle(256, 0.0, threads=1)              # no time budget: one sweep
+    assert r["cores"] == 1 and r["value"] > 0 and r["sample"].startswith("1 sweep of one 256x256")
+    assert r["sample"].endswith("oracle on 1 host thread")
+    r = bench.time_oracle(256, 10.0, max_sweeps=3, threads=2)  # the sweep cap ends it first
+    assert r["cores"] == 2 and r["sample"].startswith("3 sweeps of one 256x256")
+    assert bench.host_cpu_model()
+
+
+def test_cpu_baseline_object():
+    import bench
+    cb = bench.cpu_baseline(512, 0.0)
+    assert cb["kind"] == "oracle" and cb["unit"] == "flip/ns" and cb["value"] > 0 and cb["cores"] >= 1
+    assert "seconds" not in cb and cb["cpu_model"]
+    st = cb["single_thread"]
+    assert st["value"] > 0 and st["unit"] == "flip/ns" and st["sample"].endswith("on 1 host thread")
