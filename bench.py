@@ -33,6 +33,13 @@ T_RUNS = (1.5, 2.269185, 3.0)
 OPS_PER_SITE = 18.5
 SMS = 152
 SINGLE_THREAD_L = 4096   # lattice of the single-thread oracle figure
+# the paper's own figures, for context only (other hardware and workloads)
+PAPER_CONTEXT = {
+    "paper": "61,853 flip/ns aggregate on a Cerebras CS-2 (WSE-2) for 754 simulations (Section 3.2, Table 1)",
+    "paper_gpu": "Romero et al.'s code as the paper quotes it: 880.6 flip/ns on one H100, 585.8 on one A100, "
+                 "459 on one V100",
+    "note": "other hardware and workloads: context, not a target",
+}
 INT_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
@@ -274,7 +281,8 @@ def reference_arm(args):
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
             "config": workload_config(args),
             "cpu_baseline": cb,
-            "e2e": {"value": value, "unit": "flip/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "flip/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "context": PAPER_CONTEXT}
     print(json.dumps(line), flush=True)
 
 
@@ -432,6 +440,7 @@ def ours(args):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
+            "context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     for s in sims:

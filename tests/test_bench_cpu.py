@@ -31,6 +31,7 @@ def test_reference_line_keys_and_config():
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert cb["cpu_model"]
+    assert "61,853 flip/ns" in line["context"]["paper"]
     assert line["e2e"] == {"value": line["value"], "unit": "flip/ns", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
