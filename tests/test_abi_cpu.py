@@ -169,3 +169,25 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.ising_wolff_sweep(None, 1, None, 0) == ising.ISING_EINVAL
     assert lib.ising_sw_labels(None, 0, None, 0, None) == ising.ISING_EINVAL
     assert lib.ising_sw_get_thresholds(None, None) == ising.ISING_EINVAL
+
+
+def test_no_fallback_when_the_library_cannot_be_built():
+    # with the build failing (as without nvcc), every entry point raises, the
+    # host-only statistics too: there is no CPU path to fall back to
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2404_16990_gb300 import build, ising\n"
+        "def boom(*a, **k): raise RuntimeError('nvcc failed')\n"
+        "build.build = boom\n"
+        "ising._lib = None\n"
+        "for call in (ising.ising_version, lambda: ising.ising_workspace_bytes(64, 1),\n"
+        "             lambda: ising.ising_tau_int([1.0, 2.0, 3.0])):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except Exception as e:\n"
+        "        print('raised', type(e).__name__)\n"
+        "    else:\n"
+        "        print('returned')\n" % ROOT)
+    import sys
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300).stdout.split("\n")
+    assert [ln.split()[0] for ln in out if ln] == ["raised"] * 3, out
