@@ -326,6 +326,22 @@ def sampling_draws(seed, s, j, round_index, P=8):
     return np.array([oracle.site_random(seed, 64 * j + i, round_index, s, 4) for i in range(P * P)], np.float64)
 
 
+def train_windows(pool, seed, step, batch, P=8):
+    """The windows of training step `step`: window b comes from snapshot
+    r0 % n_snap with top-left interior site (x0, y0) = (r1 % L, r2 % L), where
+    (r0, r1, r2, r3) = Philox4x32-10 of counter (b, step, 0, 6) keyed by the
+    seed (lo32, hi32).  pool: [n_snap, L, L] spins."""
+    import oracle
+    pool = np.asarray(pool)
+    n_snap, L = pool.shape[0], pool.shape[1]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    out = []
+    for b in range(batch):
+        r = oracle.philox4x32_10([b, step, 0, 6], key)
+        out.append(extract(pool[int(r[0]) % n_snap], int(r[1]) % L, int(r[2]) % L, P))
+    return np.stack(out)
+
+
 def learned_round(sigma, flat, T, seed, s, round_index, P=8, prec="bf16"):
     """One MH patch round on lattice sigma (in place).  Uniforms: Philox
     phase 4 (sampling: counter (16 j + i/4, round, s, 4), lane i % 4) and phase

@@ -273,3 +273,24 @@ def test_learned_round_limits_with_a_uniform_proposal():
             assert acc == len(recs)
         else:
             assert any(r["dE"] > 0 for r in recs) and any(r["dE"] < 0 for r in recs)
+
+
+def test_training_windows_follow_their_draws():
+    # snapshots that differ everywhere tell which one a window came from; the
+    # ring and interior of each window are the periodic neighbourhood of its origin
+    L, n_snap, seed = 32, 5, 0x1234_5678_9ABC
+    rng = np.random.default_rng(2)
+    pool = np.where(rng.random((n_snap, L, L)) < 0.5, -1, 1).astype(np.int8)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for step in (0, 7):
+        wins = ol.train_windows(pool, seed, step, 64)
+        for b in range(64):
+            r = oracle.philox4x32_10([b, step, 0, 6], key)
+            snap, x0, y0 = int(r[0]) % n_snap, int(r[1]) % L, int(r[2]) % L
+            ys, xs = (y0 - 1 + np.arange(10)) % L, (x0 - 1 + np.arange(10)) % L
+            assert np.array_equal(wins[b], pool[snap][np.ix_(ys, xs)])
+    # over many draws every snapshot and origin row is used about equally often
+    from scipy import stats
+    snaps = [int(oracle.philox4x32_10([b, 3, 0, 6], key)[0]) % n_snap for b in range(5000)]
+    counts = np.bincount(snaps, minlength=n_snap)
+    assert stats.chisquare(counts).pvalue > 1e-3
