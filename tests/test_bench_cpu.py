@@ -61,3 +61,23 @@ def test_cpu_baseline_object():
     assert "seconds" not in cb and cb["cpu_model"]
     st = cb["single_thread"]
     assert st["value"] > 0 and st["unit"] == "flip/ns" and st["sample"].endswith("on 1 host thread")
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    # two ranks on one node: rank 0 alone times the oracle and prints one line,
+    # the other rank exits 0 without work
+    import socket
+    import sys
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--L", "256"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
