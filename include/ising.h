@@ -109,7 +109,8 @@ int ising_create_batch(ising_t* out, int n_sims, const int* Ls, const double* te
  * half-sweep; Algorithm 3's loop body).  Asynchronous on the handle's stream:
  * returns after enqueueing.  After each sweep E and M are recorded (current
  * values, trace ring, and the FP64 moment sums if measuring is on).  If a
- * bounded device-side wait of the resident kernel runs out, the next call that
+ * bounded device-side wait of the resident kernel or of the persistent
+ * streaming kernel runs out (ising_set_wait_limit_ns), the next call that
  * synchronises returns ISING_ETIMEOUT and the state is undefined.  The sweep
  * counter must stay below 2^32 (ISING_EINVAL otherwise). */
 int ising_sweep(ising_t h, int64_t n);
@@ -153,6 +154,21 @@ int ising_num_sims(ising_t h);
 
 /* Turn the accumulation of FP64 moments on (1) or off (0). */
 int ising_set_measure(ising_t h, int on);
+
+/* Bound of every device-side wait of the handle's sweep kernels, in
+ * nanoseconds of the GPU's global timer: the resident kernel's wait for the
+ * previous chunk of its lattice group and the persistent streaming kernel's
+ * grid barrier.  ns = 0 restores the default of 10 s; at most
+ * ISING_MAX_WAIT_LIMIT_NS.  A wait that runs out sets the handle's error word
+ * and its kernel returns without finishing the sweeps; from then on every
+ * synchronising call on the handle (ising_observables, ising_trace,
+ * ising_moments, ising_get_spins, ...) returns ISING_ETIMEOUT and the
+ * handle's lattices are undefined (make a new handle).  A short limit exists
+ * for testing that path: failure detection in the sense of the paper's
+ * long-running validation scans (Section 3.1), where a stalled kernel must
+ * end with an error rather than hold the GPU.  Synchronises the stream. */
+#define ISING_MAX_WAIT_LIMIT_NS 600000000000ull
+int ising_set_wait_limit_ns(ising_t h, uint64_t ns);
 
 /* Zero the moment sums. */
 int ising_reset_moments(ising_t h);
@@ -345,6 +361,21 @@ int ising_net_grad(ising_net_t net, const int8_t* host_windows, int n, float* ho
  * per-step losses go to host_losses [steps] if not NULL. */
 int ising_net_train(ising_net_t net, const void* dev_pool_words, int n_snap, int L, int64_t steps,
                     int batch, float lr, uint64_t seed, float* host_losses);
+
+/* The windows that training step `step` of ising_net_train draws: batch
+ * (<= max_windows) windows into host_windows [batch][100], by the rule given
+ * for ising_net_train (the same kernel).  Does not change the net.  For
+ * inspecting and checking the training data. */
+int ising_net_train_windows(ising_net_t net, const void* dev_pool_words, int n_snap, int L, int64_t step,
+                            int batch, uint64_t seed, int8_t* host_windows);
+
+/* One Adam step of the fp32 masters with a caller-given gradient (host
+ * [ISING_NET_PARAMS]) by the same update kernel as ising_net_train: with k
+ * the net's step count after incrementing it, m = 0.9 m + 0.1 g, v = 0.999 v
+ * + 0.001 g^2, w -= lr (m / (1 - 0.9^k)) / (sqrt(v / (1 - 0.999^k)) + 1e-8)
+ * (Kingma and Ba 2015), all in fp32; then the bf16 (and, if in use, e4m3)
+ * copies are refreshed.  Synchronises. */
+int ising_net_apply_grad(ising_net_t net, const float* host_grad, float lr);
 
 /* One learned patch round over every lattice of h (round index round_index;
  * L must be a multiple of 16, which every valid L is), on h's stream: gather

@@ -49,8 +49,10 @@ struct Control {
     long long trace_cap;         // trace entries per lattice (0 = none)
     unsigned int bar_count;      // persistent kernel: blocks arrived at the grid barrier
     unsigned int bar_gen;        // persistent kernel: grid barrier generation
-    unsigned int pad[6];
+    unsigned long long wait_limit_ns;  // bound of every device wait; 0 = the default (10 s)
+    unsigned int pad[4];
 };
+static_assert(sizeof(Control) == 64, "control block layout");
 
 // Device pointers of one handle, passed by value to kernels.
 struct DevState {
@@ -90,6 +92,7 @@ struct NetState {
     float* loss;           // scalar
     uint8_t* wq;           // e4m3 copy of the weights, scaled per layer (FP8 inference)
     float* wscale;         // [4] per-layer power-of-two weight scales of the e4m3 copy
+    int* err;              // nonzero: a bounded wait of a tensor-core kernel ran out
 };
 
 // Swendsen-Wang step: tiles of kSwTileW x kSwTileH sites (x in [64 tx,
@@ -141,6 +144,11 @@ cudaError_t launch_random_stream(uint32_t k0, uint32_t k1, uint32_t s, uint32_t 
 // Record a message for ising_last_error() and return code (ising_api.cu).
 int set_last_error(int code, const char* msg);
 
+// Metropolis acceptance threshold min(floor(2^32 exp(-dE/T)), 2^32 - 1),
+// evaluated in double precision (ising_api.cu); the one table builder of
+// every sweep path.
+uint32_t threshold_u32(double dE, double T);
+
 // Learned-proposal launch wrappers (ising_learned.cu).
 cudaError_t configure_learned_kernels();
 cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
@@ -151,6 +159,7 @@ cudaError_t launch_net_score(const NetState& ns, const int8_t* win, int n, float
                              float* lq_b, cudaStream_t stream);
 cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
                               uint32_t round_t, cudaStream_t stream);
+
 cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, const float* z,
                                 const __nv_bfloat16* h, float* grad, float* loss, cudaStream_t stream);
 cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream);

@@ -26,7 +26,13 @@ namespace ising {
 namespace {
 
 constexpr int kMaxGroupCount = 256;       // lattices per resident group
-constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
+constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;  // default bound: 10 s
+
+// The bound of a device wait: the handle's setting, else the default.
+__device__ __forceinline__ unsigned long long wait_limit(const Control* ctl) {
+    const unsigned long long v = ctl->wait_limit_ns;
+    return v != 0 ? v : kWaitLimitNs;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -246,9 +252,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(DevState st, int n_gro
         const int g = (int)(ticket % n_groups);
         const long long chunk = ticket / n_groups;
         if (tid == 0) {
-            const unsigned long long start = global_ns();
+            const unsigned long long start = global_ns(), limit = wait_limit(st.ctl);
             while ((long long)ld_acquire(&st.done[g]) < chunk) {
-                if (global_ns() - start > kWaitLimitNs) {
+                if (global_ns() - start > limit) {
                     atomicOr(&st.ctl->error, 1);
                     s_abort = 1;
                     break;
@@ -504,9 +510,9 @@ __device__ __forceinline__ bool grid_barrier(Control* ctl) {
             __threadfence();
             st_release(&ctl->bar_gen, g + 1u);
         } else {
-            const unsigned long long start = global_ns();
+            const unsigned long long start = global_ns(), limit = wait_limit(ctl);
             while (ld_acquire(&ctl->bar_gen) == g) {
-                if (global_ns() - start > kWaitLimitNs) {
+                if (global_ns() - start > limit) {
                     atomicOr(&ctl->error, 2);
                     ok = 0;
                     break;

@@ -41,10 +41,32 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-uint32_t noalloc_threshold(double dE, double T) {
-    const double v = std::ldexp(std::exp(-dE / T), 32);
-    if (v >= 4294967296.0) return 0xFFFFFFFFu;
-    return (uint32_t)std::floor(v);
+// Descriptors of up to kSetupChunk lattices, passed by value as a kernel
+// parameter: the launch copies them, so no host buffer has to outlive the
+// call and no host-to-device copy is issued.
+constexpr int kSetupChunk = 16;
+struct SetupBlock {
+    Control ctl;                  // written by the chunk with first == 0
+    int first, count;             // lattices first .. first + count - 1
+    LatDesc lat[kSetupChunk];
+    StreamLat sl[kSetupChunk];
+};
+static_assert(sizeof(SetupBlock) <= 4096, "setup block must fit the classic kernel parameter limit");
+
+// Writes one chunk of descriptors into the scratch and zeroes those
+// lattices' partial sums (device code names the array directly).
+__global__ void noalloc_setup_kernel(const __grid_constant__ SetupBlock b) {
+    unsigned char* base = g_noalloc_scratch;
+    const int i = threadIdx.x;
+    if (i == 0 && b.first == 0) *reinterpret_cast<Control*>(base + kCtlOff) = b.ctl;
+    if (i < b.count) {
+        const int k = b.first + i;
+        reinterpret_cast<LatDesc*>(base + kLatOff)[k] = b.lat[i];
+        reinterpret_cast<StreamLat*>(base + kSlatOff)[k] = b.sl[i];
+        unsigned long long* acc = reinterpret_cast<unsigned long long*>(base + kAccOff);
+        acc[2 * k] = 0ull;
+        acc[2 * k + 1] = 0ull;
+    }
 }
 
 // Device address of the scratch on the current device (set up once per device).
@@ -96,8 +118,7 @@ extern "C" int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls
     int V = 2;
     for (int i = 0; i < n_lat; ++i)
         if ((Ls[i] / 64) % 2 != 0) V = 1;
-    LatDesc lat[ISING_NOALLOC_MAX_LATTICES];
-    StreamLat sl[ISING_NOALLOC_MAX_LATTICES];
+    std::vector<SetupBlock> chunks((size_t)((n_lat + kSetupChunk - 1) / kSetupChunk));
     uint64_t off = 0, tiles = 0;
     for (int i = 0; i < n_lat; ++i) {
         const uint32_t L = (uint32_t)Ls[i], wn = L / 64;
@@ -108,9 +129,10 @@ extern "C" int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls
         d.sim = (uint32_t)i;
         d.key0 = (uint32_t)(seeds[i] & 0xFFFFFFFFull);
         d.key1 = (uint32_t)(seeds[i] >> 32);
-        d.thr0 = noalloc_threshold(4.0, temps[i]);
-        d.thr1 = noalloc_threshold(8.0, temps[i]);
-        lat[i] = d;
+        d.thr0 = threshold_u32(4.0, temps[i]);
+        d.thr1 = threshold_u32(8.0, temps[i]);
+        SetupBlock& b = chunks[(size_t)(i / kSetupChunk)];
+        b.lat[i % kSetupChunk] = d;
         off += (uint64_t)L * L / 32;
         StreamLat s{};
         s.lat = (uint32_t)i;
@@ -124,18 +146,17 @@ extern "C" int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls
         s.strips = tiles_y;
         s.item_begin = tiles;
         tiles += (uint64_t)tiles_x * tiles_y;
-        sl[i] = s;
+        b.sl[i % kSetupChunk] = s;
     }
-    Control ctl{};
-    ctl.t = (unsigned long long)t0;   // trace_cap = 0 and measure = 0: only E/M are written
-
-    cudaError_t e = cudaMemcpyAsync(base + kCtlOff, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + kLatOff, lat, n_lat * sizeof(LatDesc), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + kSlatOff, sl, n_lat * sizeof(StreamLat), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)   // partial sums start at zero
-        e = cudaMemsetAsync(base + kAccOff, 0, n_lat * 2 * sizeof(unsigned long long), stream);
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        SetupBlock& b = chunks[c];
+        b.first = (int)c * kSetupChunk;
+        b.count = std::min(kSetupChunk, n_lat - b.first);
+        b.ctl = Control{};
+        b.ctl.t = (unsigned long long)t0;   // trace_cap = 0 and measure = 0: only E/M are written
+        noalloc_setup_kernel<<<1, kSetupChunk, 0, stream>>>(b);
+    }
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_last_error(ISING_ECUDA, cudaGetErrorString(e));
 
     DevState st{};

@@ -81,6 +81,7 @@ def _load():
             "ising_lattice_size": ([vp, ctypes.c_int], ctypes.c_int),
             "ising_num_sims": ([vp], ctypes.c_int),
             "ising_set_measure": ([vp, ctypes.c_int], ctypes.c_int),
+            "ising_set_wait_limit_ns": ([vp, ctypes.c_uint64], ctypes.c_int),
             "ising_reset_moments": ([vp], ctypes.c_int),
             "ising_moments": ([vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "ising_state_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
@@ -109,6 +110,9 @@ def _load():
             "ising_net_train": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_float,
                                  ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ising_learned_round": ([vp, vp, i64, i64p], ctypes.c_int),
+            "ising_net_train_windows": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_int8)], ctypes.c_int),
+            "ising_net_apply_grad": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.c_float], ctypes.c_int),
             "ising_snapshot": ([vp, vp, sz], ctypes.c_int),
             "ising_net_accepted": ([vp, i64p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "ising_net_set_precision": ([vp, ctypes.c_int], ctypes.c_int),
@@ -286,6 +290,13 @@ def ising_set_measure(h, on: bool) -> None:
     _check(_load().ising_set_measure(h, 1 if on else 0))
 
 
+ISING_MAX_WAIT_LIMIT_NS = 600_000_000_000
+
+
+def ising_set_wait_limit_ns(h, ns: int) -> None:
+    _check(_load().ising_set_wait_limit_ns(h, int(ns)))
+
+
 def ising_reset_moments(h) -> None:
     _check(_load().ising_reset_moments(h))
 
@@ -351,6 +362,8 @@ def ising_sweep_noalloc(dev_words: int, Ls: Sequence[int], temps: Sequence[float
     La = np.ascontiguousarray(Ls, dtype=np.int32)
     T = np.ascontiguousarray(temps, dtype=np.float64)
     S = np.ascontiguousarray([int(s) for s in seeds], dtype=np.uint64)
+    if not (len(La) == len(T) == len(S)):
+        raise ValueError(f"Ls, temps and seeds must have the same length ({len(La)}, {len(T)}, {len(S)})")
     _check(_load().ising_sweep_noalloc(dev_words, len(La), _ptr(La, ctypes.c_int), _ptr(T, ctypes.c_double),
                                        _ptr(S, ctypes.c_uint64), t0, n, dev_EM, cuda_stream))
 
@@ -457,6 +470,17 @@ class IsingNet:
         _check(_load().ising_net_train(self.h, dev_pool_words, n_snap, L, steps, batch, lr, seed,
                                        _ptr(losses, ctypes.c_float)))
         return losses[:steps]
+
+    def train_windows(self, dev_pool_words: int, n_snap: int, L: int, step: int, batch: int, seed: int):
+        out = np.zeros((batch, 10, 10), dtype=np.int8)
+        _check(_load().ising_net_train_windows(self.h, dev_pool_words, n_snap, L, step, batch, seed,
+                                               _ptr(out, ctypes.c_int8)))
+        return out
+
+    def apply_grad(self, grad, lr: float) -> None:
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        assert g.size == ISING_NET_PARAMS
+        _check(_load().ising_net_apply_grad(self.h, _ptr(g, ctypes.c_float), lr))
 
     def accepted(self, n: int, reset: bool = True) -> np.ndarray:
         acc = np.zeros(max(1, n), dtype=np.int64)

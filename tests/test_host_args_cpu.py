@@ -45,6 +45,17 @@ def test_noalloc_arguments():
     _einval(sw, FAKE, [64], [2.0], [1], 0, -1, FAKE)                             # n < 0
     _einval(sw, FAKE, [64], [2.0], [1], 2**32 - 4, 8, FAKE)                      # counter past 2^32
     sw(FAKE, [64, 128], [2.0, 3.0], [1, 2], 5, 0, FAKE)                          # n = 0: nothing to do, OK
+    # the binding checks that the three host arrays agree in length before the
+    # library reads n_lat entries from each
+    for Ls, temps, seeds in (([64, 128], [2.0], [1, 2]), ([64, 128], [2.0, 3.0], [1]), ([64], [2.0, 3.0], [1, 2])):
+        with pytest.raises(ValueError):
+            sw(FAKE, Ls, temps, seeds, 0, 1, FAKE)
+
+
+def test_wait_limit_arguments():
+    _einval(ising.ising_set_wait_limit_ns, None, 1000)                           # NULL handle
+    _einval(ising.ising_set_wait_limit_ns, None, ising.ISING_MAX_WAIT_LIMIT_NS + 1)
+    assert "at most" in ising.ising_last_error()
 
 
 def test_net_workspace_bytes():
