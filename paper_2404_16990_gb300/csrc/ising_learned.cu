@@ -1418,7 +1418,9 @@ cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, co
 }
 
 cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream) {
-    const float bc1 = 1.0f - powf(0.9f, (float)step), bc2 = 1.0f - powf(0.999f, (float)step);
+    // bias corrections 1 - beta^step in double on the host: in fp32 from the
+    // rounded betas, 1 - 0.999f loses about 1e-5 of its value to cancellation
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)step)), bc2 = (float)(1.0 - std::pow(0.999, (double)step));
     adam_kernel<<<(kNParams + 255) / 256, 256, 0, stream>>>(ns.w, ns.m, ns.v, ns.g, ns.wb, lr, bc1, bc2);
     return cudaGetLastError();
 }

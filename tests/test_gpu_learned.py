@@ -61,22 +61,31 @@ def test_score_large_batch_matches_oracle_on_a_subset():
     assert np.allclose(lq[pick], ol.log_q(win[pick], zo), atol=5e-2, rtol=1e-3)
 
 
-def test_gradient_matches_oracle():
+def test_gradient_matches_oracle_elementwise():
+    """Every one of the 2945 gradient entries against the oracle's float64
+    backward pass through the same bf16 rounding points:
+    |g - g_o| <= 1e-3 |g_o| + 1e-5 max|g_o|.  The GPU sums in fp32 (30,000
+    positions per entry), which bounds the relative error near 1e-6; the
+    floor covers entries whose terms cancel to near zero, and bf16
+    activations rounded the other way at a near-tie (a change of one bf16
+    unit in one of 1.4 M activations moves an entry by about 1e-7 of its
+    scale).  The bar is ten times tighter than the 1e-2 the method needs."""
     net = ising.IsingNet(max_windows=512)
     flat = ol.init_params(9, gain=1.5)
     net.set_params(flat)
     win = rand_windows(300, 2)
     g, loss = net.grad(win)
     go = ol.grad(win, flat)
-    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
-    assert rel < 1e-2, rel
-    assert abs(loss - ol.loss(win, flat)) < 1e-3 * abs(ol.loss(win, flat)) + 1e-3
-    # every parameter block, not only the large ones
+    lo = ol.loss(win, flat)
+    assert abs(loss - lo) <= 1e-5 * abs(lo), (loss, lo)
+    tol = 1e-3 * np.abs(go) + 1e-5 * np.abs(go).max()
+    bad = np.flatnonzero(np.abs(g - go) > tol)
+    assert bad.size == 0, (bad[:8], g[bad[:8]], go[bad[:8]])
+    # every parameter block is really exercised (no block of exact zeros)
     o = 0
     for k in ol.ORDER:
         n = int(np.prod(ol.SIZES[k]))
-        if np.linalg.norm(go[o:o + n]) > 0:
-            assert np.linalg.norm(g[o:o + n] - go[o:o + n]) <= 2e-2 * np.linalg.norm(go[o:o + n]) + 1e-6, k
+        assert np.abs(go[o:o + n]).max() > 0, k
         o += n
 
 
@@ -236,6 +245,16 @@ def test_async_rounds_match_synchronous_rounds():
 
 
 def test_fp8_score_matches_oracle():
+    """FP8 (E4M3) scoring against the oracle's own FP8 mode (the same e4m3
+    rounding of weights times their power-of-two scales and of every hidden
+    activation).  Both sum in fp32 or better, so a logit differs only by
+    fp32 rounding -- |dz| <= 1e-4 (1 + |z|) -- except where some activation
+    upstream lies within that rounding of an e4m3 rounding boundary and is
+    rounded the other way; one e4m3 step (1/8 relative) of one activation
+    moves a logit by far less than 0.5.  Such near-ties are rare (about one
+    expected in this batch): at most 1 % of the positions may exceed the fp32
+    bound, and every window whose logits all meet it has log q within 1e-4
+    (1 + |log q|)."""
     net = ising.IsingNet(max_windows=128)
     flat = ol.init_params(29, gain=1.5)
     net.set_params(flat)
@@ -244,11 +263,16 @@ def test_fp8_score_matches_oracle():
     net.set_precision(ising.ISING_NET_FP8)
     lq8, z8 = net.score(win, with_z=True)
     zo, _ = ol.forward(win, flat, prec="fp8")
+    zo = zo.reshape(45, 100)
     inner = ol.interior_mask(10).ravel()
-    dz = np.abs(z8[:, inner] - zo.reshape(45, 100)[:, inner])
-    assert np.median(dz) < 1e-3 and dz.max() < 0.5, (np.median(dz), dz.max())
+    dz = np.abs(z8[:, inner] - zo[:, inner])
+    off = dz > 1e-4 * (1.0 + np.abs(zo[:, inner]))
+    assert off.mean() <= 0.01 and dz.max() < 0.5, (off.sum(), dz.max())
     assert np.abs(z8 - z16)[:, inner].max() > 1e-3          # the precision really changed
-    assert np.allclose(lq8, ol.log_q(win, zo), atol=0.5, rtol=1e-2)
+    lqo = ol.log_q(win, zo.reshape(45, 10, 10))
+    clean = ~off.any(axis=1)
+    assert clean.sum() >= 40
+    assert np.all(np.abs(lq8[clean] - lqo[clean]) <= 1e-4 * (1.0 + np.abs(lqo[clean])))
 
 
 @pytest.mark.parametrize("rnd", [0, 1])

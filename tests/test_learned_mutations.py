@@ -32,6 +32,14 @@ MUTATIONS = {
     "weight_not_transposed_in_backward": ('dH2 += shift_back(dA3 @ W["W3"][t].T, dy, dx)',
                                           'dH2 += shift_back(dA3 @ W["W3"][t], dy, dx)'),
     "adam_without_bias_correction": ("mhat = m / (1 - b1 ** step)", "mhat = m"),
+    "adam_beta2_wrong": ("def adam_step(flat, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):",
+                         "def adam_step(flat, m, v, g, step, lr, b1=0.9, b2=0.99, eps=1e-8):"),
+    "adam_beta1_wrong": ("def adam_step(flat, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):",
+                         "def adam_step(flat, m, v, g, step, lr, b1=0.8, b2=0.999, eps=1e-8):"),
+    "adam_eps_inside_root": ("flat = (flat - lr * mhat / (np.sqrt(vhat) + eps)).astype(np.float32)",
+                             "flat = (flat - lr * mhat / np.sqrt(vhat + eps)).astype(np.float32)"),
+    "adam_second_moment_unsquared": ("v = (b2 * v + (1 - b2) * g * g).astype(np.float32)",
+                                     "v = (b2 * v + (1 - b2) * np.abs(g)).astype(np.float32)"),
     "patch_offsets": ("OFFSETS = [(0, 0), (8, 8), (0, 8), (8, 0)]", "OFFSETS = [(0, 0), (8, 8), (0, 8), (0, 8)]"),
     "round_dm_sign": ("dMt += int(new[j][1:P + 1, 1:P + 1].astype(np.int64).sum() - wins[j]",
                       "dMt -= int(new[j][1:P + 1, 1:P + 1].astype(np.int64).sum() - wins[j]"),
@@ -49,6 +57,7 @@ CHECKS = [
     ("local_energy", lambda: pins.test_local_energy_matches_full_hamiltonian()),
     ("patch_tiling", lambda: pins.test_patch_origins_tile_the_lattice_and_rings_avoid_interiors()),
     ("adam", lambda: pins.test_adam_first_step_is_signed_lr()),
+    ("adam_closed_forms", lambda: pins.test_adam_closed_forms_fix_betas_and_epsilon()),
     ("gradient_fd", lambda: pins.test_gradient_matches_finite_differences()),
     ("sampler_path_4", lambda: pins.test_sampler_path_probability_is_q(4, 2.0)),
     ("sampler_path_10", lambda: pins.test_sampler_path_probability_is_q(10, 0.7)),

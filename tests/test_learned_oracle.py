@@ -141,6 +141,35 @@ def test_adam_first_step_is_signed_lr():
     assert np.allclose(p[:3], -0.01 * np.sign(g[:3]), rtol=1e-4) and p[3] == 0.0
 
 
+def test_adam_closed_forms_fix_betas_and_epsilon():
+    """Adam's later steps and its epsilon, against values worked out by hand
+    from the definition (Kingma & Ba 2015, bias-corrected moments; beta1 =
+    0.9, beta2 = 0.999, eps = 1e-8 outside the square root):
+    * gradient 1 then 0: after step 2, m = 0.09 and v = 0.000999, so the
+      second update is lr (0.09/0.19) / sqrt(0.000999/0.001999) = lr (9/19) /
+      sqrt(999/1999) = 0.670058... lr (a beta2 of 0.99 would give 0.6716 lr,
+      a beta1 of 0.8 0.6287 lr);
+    * gradient 1, 0, 0: the third update is lr (0.081/0.271) /
+      sqrt(0.000998001/0.002997001) = 0.517957... lr;
+    * a first gradient of 1e-8: the update is lr 1e-8 / (1e-8 + 1e-8) =
+      lr / 2 (epsilon inside the root would give about lr 1e-4)."""
+    lr = 0.01
+    z = np.zeros(3, np.float32)
+    g1 = np.array([1.0, -1.0, 1e-8], np.float32)
+    p1, m, v = ol.adam_step(z, z, z, g1, 1, lr)
+    assert np.allclose(p1[:2], [-lr, lr], rtol=1e-6)
+    assert abs(p1[2] + lr / 2) < 1e-6 * lr
+    g0 = np.zeros(3, np.float32)
+    p2, m, v = ol.adam_step(p1, m, v, g0, 2, lr)
+    second = (9.0 / 19.0) / math.sqrt(999.0 / 1999.0)
+    assert abs((p1[0] - p2[0]) / lr - second) < 1e-5 and abs((p2[1] - p1[1]) / lr - second) < 1e-5
+    assert abs(second - 0.670058) < 1e-6
+    p3, m, v = ol.adam_step(p2, m, v, g0, 3, lr)
+    third = (0.081 / 0.271) / math.sqrt(0.000998001 / 0.002997001)
+    assert abs((p2[0] - p3[0]) / lr - third) < 1e-5
+    assert abs(third - 0.517957) < 1e-6
+
+
 def test_learned_round_runs_and_keeps_energy_bookkeeping():
     L, T, seed = 32, 2.3, 3
     s = oracle.init(L, seed, 0)
