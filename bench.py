@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the effective-samples comparison (plain / learned / Swendsen-Wang)")
+    ap.add_argument("--learned-units", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -287,6 +290,39 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# the metric's second half: effective samples per second, learned vs plain
+# ---------------------------------------------------------------------------
+def learned_vs_plain(units: int = 20000) -> dict:
+    """Effective independent |M| and E samples per second of plain sweeps,
+    the learned patch proposal (trained on the GPU on plain-sampler
+    snapshots) and Swendsen-Wang steps, on the learned-proposal workload at
+    T_c: 64 replicas of 256^2, one equilibrated start, `units` units per
+    chain; tau_int from the library's Madras-Sokal window, seconds from CUDA
+    events.  A failure is reported in the record, not raised."""
+    try:
+        from paper_2404_16990_gb300 import learned_study
+        r = learned_study.effective_samples(T=T_RUNS[1], units=units)
+    except Exception as e:  # the throughput line stands on its own
+        return {"error": f"{type(e).__name__}: {e}"}
+    chains = {"plain": r["plain"], "learned": r["learned"], "swendsen_wang": r["swendsen_wang"]}
+    return {
+        "workload": f"64 replicas of 256x256 at T={T_RUNS[1]}, random start equilibrated by 500 Swendsen-Wang "
+                    f"steps and 2000 sweeps; learned net trained 1500 Adam steps on {r['train_pool']} plain-sampler "
+                    f"snapshots; {units} units per chain (learned unit = patch round + sweep)",
+        "metric": "effective independent |M| samples/s (tau_int, Madras-Sokal window)",
+        "eff_samples_per_s_absM": {k: v["eff_samples_per_s_absM"] for k, v in chains.items()},
+        "eff_samples_per_s_E": {k: v["eff_samples_per_s_E"] for k, v in chains.items()},
+        "learned_over_plain_absM": r["gain_eff_samples_absM"],
+        "sw_over_plain_absM": r["gain_sw_eff_samples_absM"],
+        "tau_int_absM": {k: v["tau_int_absM"] for k, v in chains.items()},
+        "units_per_s": {k: v["units_per_s"] for k, v in chains.items()},
+        "acceptance": r["acceptance"], "acceptance_untrained": r["acceptance_untrained"],
+        "agree_sigma_learned_vs_plain": {"abs_m": r["agree_abs_m_sigma"], "e": r["agree_e_sigma"]},
+        "timing": "CUDA events on the chains' stream; training and set-up outside the timed chains",
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def ours(args):
@@ -418,6 +454,9 @@ def ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "l16384":
         cpu = cpu_baseline(L, args.cpu_seconds)
+    learned = None
+    if rank == 0 and ws == 1 and not args.no_learned and args.workload == "l16384":
+        learned = learned_vs_plain(args.learned_units)
 
     if rank == 0:
         cfg = workload_config(args, rank)
@@ -437,6 +476,7 @@ def ours(args):
                          "kernel": kname, "ops_per_site": OPS_PER_SITE,
                          "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz"},
             "cpu_baseline": cpu,
+            "learned_vs_plain": learned,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),

@@ -160,6 +160,49 @@ def run_temperature(T: float, L: int = 256, replicas: int = 64, burn: int = 2000
     return res
 
 
+def effective_samples(T: float = T_CRITICAL, L: int = 256, replicas: int = 64, units: int = 20000,
+                      sw_steps: int = 5000, train_steps: int = 1500, n_snap: int = 20000, burn: int = 2000,
+                      seed: int = 2024) -> dict:
+    """Effective independent |M| (and E) samples per second of three chains
+    from one equilibrated state: plain sweeps, the learned proposal (one
+    patch round + one sweep per unit) and Swendsen-Wang steps; tau_int by the
+    library's Madras-Sokal window per replica, seconds by CUDA events on the
+    chains' stream.  Returns the learned-vs-plain record of run_temperature
+    with a "swendsen_wang" entry and the two ratios added."""
+    import torch
+    res = run_temperature(T, L=L, replicas=replicas, burn=burn, n_snap=n_snap, train_steps=train_steps,
+                          units=units, seed=seed, verbose=False)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(dev)
+    N = L * L
+    with torch.cuda.stream(stream):
+        sim = ising.IsingSim(L, [T] * replicas, seed, trace_cap=sw_steps, stream=stream)
+        sim.sw_sweep(500)
+        sim.sweep(burn)
+        sim.set_graph(True)
+        sim.sw_sweep(10)                                 # scratch and graph set up outside the timed region
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.sw_sweep(sw_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        secs = e0.elapsed_time(e1) / 1e3
+        E, M = sim.trace(sw_steps)
+    tm, tm_err = _tau(np.abs(M).astype(np.float64))
+    te, te_err = _tau(E.astype(np.float64))
+    m, dm, e, de = _obs_stats(E, M, N)
+    res["swendsen_wang"] = {"units": sw_steps, "seconds": secs, "units_per_s": sw_steps / secs,
+                            "tau_int_absM": tm, "tau_int_absM_err": tm_err, "tau_int_E": te, "tau_int_E_err": te_err,
+                            "mean_abs_m": m, "mean_abs_m_err": dm, "mean_e": e, "mean_e_err": de,
+                            "eff_samples_per_s_absM": replicas * sw_steps / (2 * tm) / secs,
+                            "eff_samples_per_s_E": replicas * sw_steps / (2 * te) / secs}
+    p = res["plain"]
+    res["gain_sw_eff_samples_absM"] = res["swendsen_wang"]["eff_samples_per_s_absM"] / p["eff_samples_per_s_absM"]
+    res["gain_sw_eff_samples_E"] = res["swendsen_wang"]["eff_samples_per_s_E"] / p["eff_samples_per_s_E"]
+    sim.close()
+    return res
+
+
 def round_bench(rounds: int = 20, L: int = 256, replicas: int = 64, precision: int = 0, seed: int = 7) -> dict:
     """Device time of learned rounds alone (no training: seeded initial net) on
     `replicas` lattices of side L at T_c."""
