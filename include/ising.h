@@ -321,14 +321,17 @@ void ising_net_destroy(ising_net_t net);
  * ISING_NET_BF16 as above, or ISING_NET_FP8: weights enter as
  * e4m3(W * s_l) with s_l = 2^floor(log2(448 / max|W of layer l|)) (layers 1..4),
  * hidden activations as e4m3(relu(.)) (round to nearest even, saturating),
- * products summed in fp32 (mma.sync e4m3, K = 32: taps 0+1, 2+3, 4) and
- * divided by s_l before the fp32 bias.  The MH correction evaluates log q of
- * x and x' with one and the same kernel.  In FP8 the proposal is drawn with
- * that kernel's logits too; in BF16 it is drawn by a separate (wavefront)
- * kernel whose logits equal the scoring kernel's up to the order of the fp32
- * sums.  Either precision therefore samples the Boltzmann distribution up to
- * a relative bias of about 1e-6 (and the 2^-32 quantization of the sampling
- * thresholds); FP8 changes the acceptance rate and the cost. */
+ * products summed in fp32 and divided by s_l before the fp32 bias.  Scoring
+ * (ising_net_score, and both log q of a round) runs on the tcgen05 tensor
+ * cores in either precision (one MMA per tap in BF16, one per pair of taps
+ * in FP8); the MH correction evaluates log q of x and x' in one launch of
+ * that kernel.  The proposal is drawn by a separate kernel (BF16: wavefront
+ * sampler; FP8: sequential sampler) whose logits equal the scoring kernel's
+ * up to the order of the fp32 sums.  Either precision therefore samples the
+ * Boltzmann distribution up to a relative bias of about 1e-6 (and the 2^-32
+ * quantization of the sampling thresholds); FP8 changes the acceptance rate
+ * and the cost.  A bounded wait of the scoring kernel that runs out (1 s)
+ * makes the next synchronising net call return ISING_ETIMEOUT. */
 #define ISING_NET_BF16 0
 #define ISING_NET_FP8 1
 int ising_net_set_precision(ising_net_t net, int precision);

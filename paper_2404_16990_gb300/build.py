@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "libising")
 LIB = os.path.join(HERE, "libising.so")
 SOURCES = ["ising_kernels.cu", "ising_api.cu", "ising_stats.cpp", "ising_noalloc.cu", "ising_learned.cu",
-           "ising_cluster.cu", "ising3d.cu"]
+           "ising_learned_tc.cu", "ising_cluster.cu", "ising3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-I" + os.path.join(ROOT, "include")]

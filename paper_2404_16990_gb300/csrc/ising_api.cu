@@ -1286,9 +1286,9 @@ int net_refresh_fp8(ising_net* net) {
     return ISING_OK;
 }
 
+// log q (and logits) of n windows on the tensor cores, in the net's precision
 cudaError_t net_score(ising_net* net, const int8_t* win, int n, float* lq, float* z, cudaStream_t st) {
-    if (net->precision == ISING_NET_FP8) return launch_net_forward_fp8(net->ns, win, n, lq, z, st);
-    return launch_net_score(net->ns, win, n, lq, z, nullptr, nullptr, st);   // all positions at once
+    return launch_net_score_tc(net->ns, net->precision == ISING_NET_FP8, win, n, lq, z, nullptr, nullptr, st);
 }
 
 // ISING_ETIMEOUT if a bounded wait of a tensor-core kernel ran out (reads the
@@ -1537,16 +1537,13 @@ int ising_learned_round(ising_t h, ising_net_t net, int64_t round_index, int64_t
         CUDA_TRY(cudaMemsetAsync(net->accepted, 0, (size_t)h->n * 8, h->stream), "zero counters");
     CUDA_TRY(launch_gather_patches(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->keys, h->stream),
              "gather patches");
-    // BF16: the sampler's own log q is not needed (both patches are scored below)
+    // the sampler's own log q is not needed: both patches are scored below
     CUDA_TRY(net_sample(net, net->win2, nwin, net->precision == ISING_NET_FP8 ? net->lq2 : nullptr, rt, h->stream),
              "sample");
-    // log q of the current and of the proposed patch from the same function:
-    // in BF16 both come from the position-parallel scoring kernel (the
-    // sampler's own log q is replaced), in FP8 both from the sequential kernel
-    if (net->precision == ISING_NET_FP8)
-        CUDA_TRY(net_score(net, net->win, nwin, net->lq, nullptr, h->stream), "score");
-    else
-        CUDA_TRY(launch_net_score(net->ns, net->win, nwin, net->lq, nullptr, net->win2, net->lq2, h->stream), "score");
+    // log q of the current and of the proposed patch from the same function,
+    // in one launch of the tensor-core scoring kernel (in the net's precision)
+    CUDA_TRY(launch_net_score_tc(net->ns, net->precision == ISING_NET_FP8, net->win, nwin, net->lq, nullptr, net->win2,
+                                 net->lq2, h->stream), "score");
     CUDA_TRY(launch_mh_apply(h->st, net->ll, h->n, nwin, ox, oy, net->win, net->win2, net->lq, net->lq2, rt,
                              net->accepted, h->stream), "accept");
     if (host_accepted) {

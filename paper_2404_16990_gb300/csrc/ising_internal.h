@@ -153,20 +153,18 @@ uint32_t threshold_u32(double dE, double T);
 cudaError_t configure_learned_kernels();
 cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
                                __nv_bfloat16* h, cudaStream_t stream);
-// Teacher-forced log q (and logits z if given) of n windows; with win_b also
-// the log q of the n windows at win_b into lq_b, in the same launch.
-cudaError_t launch_net_score(const NetState& ns, const int8_t* win, int n, float* lq, float* z, const int8_t* win_b,
-                             float* lq_b, cudaStream_t stream);
 cudaError_t launch_net_sample(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
                               uint32_t round_t, cudaStream_t stream);
-
+// Teacher-forced log q on the tcgen05 tensor cores (ising_learned_tc.cu), in
+// BF16 or FP8: windows [0, n) of win (log q to lq, logits to z if given) and,
+// with win_b, [0, n) of win_b (log q to lq_b), in one launch.
+cudaError_t launch_net_score_tc(const NetState& ns, bool fp8, const int8_t* win, int n, float* lq, float* z,
+                                const int8_t* win_b, float* lq_b, cudaStream_t stream);
 cudaError_t launch_net_backward(const NetState& ns, const int8_t* win, int n, const float* z,
                                 const __nv_bfloat16* h, float* grad, float* loss, cudaStream_t stream);
 cudaError_t launch_adam(const NetState& ns, float lr, int step, cudaStream_t stream);
 cudaError_t launch_to_bf16(const NetState& ns, cudaStream_t stream);
 cudaError_t launch_to_fp8(const NetState& ns, cudaStream_t stream);
-cudaError_t launch_net_forward_fp8(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
-                                   cudaStream_t stream);
 cudaError_t launch_net_sample_fp8(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
                                   uint32_t round_t, cudaStream_t stream);
 cudaError_t launch_train_windows(const uint32_t* pool, int n_snap, uint32_t L, int nwin, uint64_t seed,

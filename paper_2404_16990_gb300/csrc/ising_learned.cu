@@ -9,13 +9,17 @@
 // include/ising.h (ising_net_* and ising_learned_round).
 //
 // Tensor cores: every layer of the net is a masked 3x3 convolution, i.e. a
-// contraction over (tap, input channel).  The kernels run it as
-// mma.sync.m16n8k16 BF16 x BF16 -> FP32: the M dimension holds the windows of
-// one warp (8 of the 16 rows, for twice the warps in flight on this
-// latency-bound sequence), K = 16 input channels of one tap (a k-step per tap),
-// N = 16 output channels (two n-tiles).  Positions are visited in raster order, so each
-// window position's activations are computed once, from already final earlier
-// positions: sampling, scoring and the training forward are the same code.
+// contraction over (tap, input channel).  Teacher-forced scoring of known
+// windows -- every position at once, M = 128 rows per window -- runs on the
+// tcgen05 tensor cores (ising_learned_tc.cu).  The kernels here are the
+// sequential ones: the training forward (which also keeps the activations for
+// the backward pass) and the samplers, whose positions depend on each other.
+// They run mma.sync (BF16 m16n8k16, E4M3 m16n8k32, FP32 accumulate), whose
+// register-level hand-off from one layer's accumulator fragment to the next
+// layer's operand fragment suits their short dependent chains: the M dimension
+// holds the windows of one warp (8 of the 16 rows in the sequential forward),
+// K = 16 input channels of one tap (a k-step per tap), N = 16 output channels
+// (two n-tiles).
 #include "../../include/ising.h"
 #include "ising_internal.h"
 #include "ising_device.cuh"
@@ -276,37 +280,19 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_kernel(NetPtrs net, con
 }
 
 // ---------------------------------------------------------------------------
-// Teacher-forced scoring of given windows, all positions at once.  With the
-// window known, every layer is a masked 3x3 convolution over known inputs --
-// an implicit GEMM with M = positions, K = (tap, input channel), N = 16 -- so
-// nothing is sequential.  One warp per window at a time, persistent over
-// windows (weights stay in registers).
-//
-// Padded layout: position (r, c) is row (r + 1) * 11 + c + 1 of a buffer of
-// 124 rows; rows 0 .. 11 and every multiple of 11 are zero (the column left
-// of a window row is the one right of the previous), so every input outside
-// the window is a zero row and tap (dy, dx) of row q is row q + 11 dy + dx.
-// A layer is seven M-tiles of 16 rows (rows 12 .. 123); the A fragment of a
-// tap is a plain ldmatrix at a constant row offset (eight consecutive rows
-// per phase at a 48-byte stride: no bank conflicts); the epilogue (bias,
-// relu, bf16) writes zeros on the pad rows and goes back by stmatrix.  The
-// layer-1 input (16 features of every row) is gathered at constant offsets
-// from two padded copies of the window's spins, interior sites only and
-// ring sites only.  Layer 4 is one n8 mma per tile giving u[t][q] = H3[q] .
-// W4[t]; the logit is z(q) = b4 + sum_t u[t][q + off_t].
-// Same masks, weights, bf16 rounding points and fp32 accumulation as the
-// sequential kernels; only the order of the fp32 sums differs.
+// Padded window layout shared by the sampler: position (r, c) is row
+// (r + 1) * 11 + c + 1 of a buffer whose rows 0 .. 11 and every multiple of 11
+// are zero (the column left of a window row is the one right of the
+// previous), so every input outside the window is a zero row and tap (dy, dx)
+// of row q is row q + 11 dy + dx.  Activation rows are 24 bf16 (16 channels +
+// 8 padding, 48 bytes: 16-byte aligned, conflict-free ldmatrix phases).
+// (Teacher-forced scoring of known windows runs on the tcgen05 tensor cores,
+// ising_learned_tc.cu.)
 // ---------------------------------------------------------------------------
-constexpr int kWarpsScore = 4;
-constexpr int kMTiles = 7;
 constexpr int kPW = kS + 1;                                      // padded row pitch (11)
 constexpr int kRow0 = kPW + 1;                                   // row of position (0, 0): 12
-constexpr int kPRows = kRow0 + 16 * kMTiles;                     // 124 buffer rows
 constexpr int kRowBytes = kRowH * 2;                             // 48: rows stay 16-byte aligned
-constexpr int kScoreH = kPRows * kRowBytes;                      // one activation buffer (5952 bytes)
-constexpr int kSpinRows = kPRows + kPW + 1;                      // padded spins, room for dy = +1 taps (136)
-constexpr int kScoreWarpSmem = 2 * kScoreH + 2 * 2 * kSpinRows;  // + interior and ring spins (12448)
-constexpr int kScoreSmem = kWarpsScore * kScoreWarpSmem;
+constexpr int kSpinRows = kRow0 + 112 + kPW + 1;                 // padded spins, room for dy = +1 taps (136)
 
 __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
     uint32_t r;
@@ -321,214 +307,7 @@ __device__ __forceinline__ void stmatrix_x4(uint32_t addr, uint32_t r0, uint32_t
     asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};\n"
                  :: "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3) : "memory");
 }
-__host__ __device__ constexpr int tap_off(int t) {                 // mask-B taps in the padded layout
-    return t < 3 ? -kPW + t - 1 : (t == 3 ? -1 : 0);
-}
 __device__ __forceinline__ int padded_row(int p) { return p + p / kS + kRow0; }
-
-// Windows [0, n) come from win_a (log q to lq_a, logits to z_a if given),
-// windows [n, 2n) from win_b when it is given (log q to lq_b).
-__global__ void __launch_bounds__(kWarpsScore * 32, 4) ar_score_kernel(NetPtrs net, const int8_t* win_a, float* lq_a,
-                                                                      float* z_a, const int8_t* win_b, float* lq_b,
-                                                                      int n) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    unsigned char* base = smem + warp * kScoreWarpSmem;
-    const uint32_t h0 = (uint32_t)__cvta_generic_to_shared(base);
-    const uint32_t hbase[2] = {h0, h0 + kScoreH};
-    uint16_t* s_in = reinterpret_cast<uint16_t*>(base + 2 * kScoreH);  // bf16 bits: interior spins
-    uint16_t* s_ring = s_in + kSpinRows;                                 // bf16 bits: ring spins
-    for (int i = lane; i < 2 * kScoreH / 4; i += 32) reinterpret_cast<uint32_t*>(base)[i] = 0u;
-    for (int i = lane; i < kSpinRows; i += 32) s_in[i] = s_ring[i] = 0;
-
-    uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[2];
-    load_b(net.wb + kOffW1, kC, 0, kC, bw1[0]);
-    load_b(net.wb + kOffW1, kC, 8, kC, bw1[1]);
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        load_b(net.wb + kOffW2 + t * 256, kC, 0, kC, bw2[t][0]);
-        load_b(net.wb + kOffW2 + t * 256, kC, 8, kC, bw2[t][1]);
-        load_b(net.wb + kOffW3 + t * 256, kC, 0, kC, bw3[t][0]);
-        load_b(net.wb + kOffW3 + t * 256, kC, 8, kC, bw3[t][1]);
-    }
-    {   // layer 4 as K = 16 channels x N = 5 taps (columns 5..7 zero): B(k, t) = W4[t][k]
-        auto at = [&](int k) -> float { return g < 5 ? __bfloat162float(net.wb[kOffW4 + g * kC + k]) : 0.0f; };
-        bw4[0] = pack_bf16(at(2 * tq), at(2 * tq + 1));
-        bw4[1] = pack_bf16(at(2 * tq + 8), at(2 * tq + 9));
-    }
-    float bias[3][2][2];
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int co = nt * 8 + 2 * tq + e;
-            bias[0][nt][e] = net.wf[kOffB1 + co];
-            bias[1][nt][e] = net.wf[kOffB2 + co];
-            bias[2][nt][e] = net.wf[kOffB3 + co];
-        }
-    const float b4 = net.wf[kOffB4];
-    // pad rows among this lane's C-fragment rows: bit 2 mt + h for row kRow0 + 16 mt + g + 8 h
-    uint32_t padmask = 0;
-#pragma unroll
-    for (int mt = 0; mt < kMTiles; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = kRow0 + 16 * mt + g + 8 * h;
-            if (q >= kRow0 + kS * kPW - 1 || q % kPW == 0) padmask |= 1u << (2 * mt + h);
-        }
-    // this lane's layer-1 feature pair (2j, 2j+1) and row within a group of four
-    const int fj = lane & 7, fsub = lane >> 3;
-    int f_lo, f_hi;                 // element offsets from s_in
-    uint32_t fmask;
-    {
-        const int k0 = 2 * fj, k1 = k0 + 1;
-        const int kind0 = c_feat[k0][2], kind1 = c_feat[k1][2];
-        f_lo = (kind0 == 1 ? kSpinRows : 0) + (kind0 == 2 ? 0 : c_feat[k0][0] * kPW + c_feat[k0][1]);
-        f_hi = (kind1 == 1 ? kSpinRows : 0) + (kind1 == 2 ? 0 : c_feat[k1][0] * kPW + c_feat[k1][1]);
-        fmask = (kind0 == 2 ? 0u : 0xFFFFu) | (kind1 == 2 ? 0u : 0xFFFF0000u);
-    }
-    __syncwarp();
-
-    const int lrow = lane & 15;
-    const uint32_t lcol = (uint32_t)(lane >> 4) * 16u;
-    auto arow = [&](uint32_t buf, int q) -> uint32_t { return buf + (uint32_t)(q + lrow) * kRowBytes + lcol; };
-    // accumulators start at the bias; relu and bf16 rounding in one conversion; pad rows get zeros
-    auto init = [&](int layer, float (&d)[2][4]) {
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            d[nt][0] = bias[layer][nt][0]; d[nt][1] = bias[layer][nt][1];
-            d[nt][2] = bias[layer][nt][0]; d[nt][3] = bias[layer][nt][1];
-        }
-    };
-    auto epilogue = [&](uint32_t dst, int mt, const float (&d)[2][4]) {
-        const bool p0 = (padmask >> (2 * mt)) & 1u, p1 = (padmask >> (2 * mt + 1)) & 1u;
-        const uint32_t r0 = p0 ? 0u : pack_bf16_relu(d[0][0], d[0][1]);
-        const uint32_t r1 = p1 ? 0u : pack_bf16_relu(d[0][2], d[0][3]);
-        const uint32_t r2 = p0 ? 0u : pack_bf16_relu(d[1][0], d[1][1]);
-        const uint32_t r3 = p1 ? 0u : pack_bf16_relu(d[1][2], d[1][3]);
-        stmatrix_x4(arow(dst, kRow0 + 16 * mt), r0, r1, r2, r3);
-    };
-
-    const int total = win_b ? 2 * n : n;
-    const int stride = gridDim.x * kWarpsScore;
-    // this lane's spins (positions lane + 32 i) of a window, fetched one window ahead
-    auto fetch = [&](int w, int8_t (&v)[4]) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = 0;
-        if (w >= total) return;
-        const int8_t* src = w >= n ? win_b + (size_t)(w - n) * kNPos : win_a + (size_t)w * kNPos;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (lane + 32 * i < kNPos) v[i] = src[lane + 32 * i];
-    };
-    int8_t next[4];
-    fetch(blockIdx.x * kWarpsScore + warp, next);
-    for (int w = blockIdx.x * kWarpsScore + warp; w < total; w += stride) {
-        const bool second = w >= n;
-        const int wi = second ? w - n : w;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int p = lane + 32 * i;
-            if (p < kNPos) {
-                const uint16_t v = next[i] > 0 ? 0x3F80u : (next[i] < 0 ? 0xBF80u : 0u);
-                const bool in = interior(p / kS, p % kS);
-                s_in[padded_row(p)] = in ? v : (uint16_t)0;
-                s_ring[padded_row(p)] = in ? (uint16_t)0 : v;
-            }
-        }
-        fetch(w + stride, next);
-        __syncwarp();
-        // layer-1 input rows 12 .. 123 into buffer 1
-#pragma unroll 4
-        for (int i = 0; i < 16 * kMTiles / 4; ++i) {
-            const int q = kRow0 + 4 * i + fsub;
-            const uint32_t v = ((uint32_t)s_in[f_lo + q] | ((uint32_t)s_in[f_hi + q] << 16)) & fmask;
-            *reinterpret_cast<uint32_t*>(base + kScoreH + q * kRowBytes + fj * 4) = v;
-        }
-        __syncwarp();
-        // Every layer is software-pipelined over the M-tiles: the ldmatrix of
-        // tile mt + 1 is issued before the mma and the stores of tile mt (they
-        // read the previous layer's buffer only).
-        // layer 1: buffer 1 -> buffer 0
-        {
-            uint32_t a[2][4];
-            ldmatrix_x4(a[0], arow(hbase[1], kRow0));
-#pragma unroll
-            for (int mt = 0; mt < kMTiles; ++mt) {
-                if (mt + 1 < kMTiles) ldmatrix_x4(a[(mt + 1) & 1], arow(hbase[1], kRow0 + 16 * (mt + 1)));
-                float d[2][4];
-                init(0, d);
-                mma16816(d[0], a[mt & 1], bw1[0]);
-                mma16816(d[1], a[mt & 1], bw1[1]);
-                epilogue(hbase[0], mt, d);
-            }
-        }
-        __syncwarp();
-        // layers 2 and 3: five mask-B taps each, 0 -> 1 -> 0
-#pragma unroll
-        for (int layer = 1; layer < 3; ++layer) {
-            const uint32_t src = hbase[(layer - 1) & 1], dst = hbase[layer & 1];
-            auto gather = [&](uint32_t (&at)[5][4], int mt) {
-#pragma unroll
-                for (int t = 0; t < 5; ++t) ldmatrix_x4(at[t], arow(src, kRow0 + 16 * mt + tap_off(t)));
-            };
-            uint32_t at[2][5][4];
-            gather(at[0], 0);
-#pragma unroll
-            for (int mt = 0; mt < kMTiles; ++mt) {
-                if (mt + 1 < kMTiles) gather(at[(mt + 1) & 1], mt + 1);
-                float d[2][4];
-                init(layer, d);
-#pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    if (layer == 1) { mma16816(d[0], at[mt & 1][t], bw2[t][0]); mma16816(d[1], at[mt & 1][t], bw2[t][1]); }
-                    else { mma16816(d[0], at[mt & 1][t], bw3[t][0]); mma16816(d[1], at[mt & 1][t], bw3[t][1]); }
-                }
-                epilogue(dst, mt, d);
-            }
-            __syncwarp();
-        }
-        // layer 4: u[t][q] = H3[q] . W4[t] into buffer 1 from its row 12 on (rows
-        // 0 .. 11 of buffer 1 stay zero for the next window's layer 3), kPRows
-        // floats per tap; u rows 0 .. 11 zero, pad rows zero since H3 is zero there
-        float* u = reinterpret_cast<float*>(base + kScoreH + kRow0 * kRowBytes);
-        {
-            uint32_t a[2][4];
-            ldmatrix_x4(a[0], arow(hbase[0], kRow0));
-#pragma unroll
-            for (int mt = 0; mt < kMTiles; ++mt) {
-                if (mt + 1 < kMTiles) ldmatrix_x4(a[(mt + 1) & 1], arow(hbase[0], kRow0 + 16 * (mt + 1)));
-                float d4[4] = {0.f, 0.f, 0.f, 0.f};
-                mma16816(d4, a[mt & 1], bw4);
-                const int c0 = 2 * tq, q = kRow0 + 16 * mt + g;     // columns c0, c0 + 1 of rows q, q + 8
-                if (c0 < 5) { u[c0 * kPRows + q] = d4[0]; u[c0 * kPRows + q + 8] = d4[2]; }
-                if (c0 + 1 < 5) { u[(c0 + 1) * kPRows + q] = d4[1]; u[(c0 + 1) * kPRows + q + 8] = d4[3]; }
-            }
-        }
-        for (int i = lane; i < 5 * kRow0; i += 32) u[(i / kRow0) * kPRows + i % kRow0] = 0.0f;
-        __syncwarp();
-        auto logit = [&](int q) -> float {
-            float z = b4;
-#pragma unroll
-            for (int t = 0; t < 5; ++t) z += u[t * kPRows + q + tap_off(t)];
-            return z;
-        };
-        // log q: the 64 interior sites, two per lane; the spin from its bf16 bits (+-1 exactly)
-        float lq_acc = 0.0f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = lane + 32 * h, q = (2 + j / kP) * kPW + 2 + j % kP;   // site (1 + j/8, 1 + j%8)
-            lq_acc += log_sigmoid(__uint_as_float((uint32_t)s_in[q] << 16) * logit(q));
-        }
-        if (!second && z_a)
-            for (int p = lane; p < kNPos; p += 32) z_a[(size_t)wi * kNPos + p] = logit(padded_row(p));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lq_acc += __shfl_down_sync(0xffffffffu, lq_acc, o);
-        if (lane == 0) (second ? lq_b : lq_a)[wi] = lq_acc;
-        __syncwarp();                   // the buffers are rewritten by the next window
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Autoregressive sampling by wavefronts.  The logit of position (r, c)
@@ -1349,8 +1128,6 @@ cudaError_t configure_learned_kernels() {
     cudaError_t e = cudaFuncSetAttribute(ar_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kWarpsFwd * kWarpSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ar_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem);
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ar_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmpSmem);
     const int bwd = (((kNParams + 3) / 4) * 4 + kWarpsBwd * 2 * kNPos * kC) * (int)sizeof(float);
     if (e == cudaSuccess)
@@ -1358,29 +1135,11 @@ cudaError_t configure_learned_kernels() {
     return e;
 }
 
-cudaError_t launch_net_score(const NetState& ns, const int8_t* win, int n, float* lq, float* z, const int8_t* win_b,
-                             float* lq_b, cudaStream_t stream) {
-    if (n <= 0) return cudaSuccess;
-    NetPtrs np{ns.wb, ns.w};
-    const int total = win_b ? 2 * n : n;
-    const int blocks = std::min((total + kWarpsScore - 1) / kWarpsScore, device_sm_count() * 4);
-    ar_score_kernel<<<blocks, kWarpsScore * 32, kScoreSmem, stream>>>(np, win, lq, z, win_b, lq_b, n);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, float* lq, float* z, __nv_bfloat16* h,
                                cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     NetPtrs np{ns.wb, ns.w};
     ar_net_kernel<<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmem, stream>>>(np, win, n, lq, z, h);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_net_forward_fp8(const NetState& ns, const int8_t* win, int n, float* lq, float* z,
-                                   cudaStream_t stream) {
-    if (n <= 0) return cudaSuccess;
-    ar_net_fp8_kernel<0><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmemQ, stream>>>(
-        ns.wq, ns.wscale, ns.w, const_cast<int8_t*>(win), n, lq, z, nullptr, 0u);
     return cudaGetLastError();
 }
 
