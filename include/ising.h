@@ -325,9 +325,9 @@ void ising_net_destroy(ising_net_t net);
  * (ising_net_score, and both log q of a round) runs on the tcgen05 tensor
  * cores in either precision (one MMA per tap in BF16, one per pair of taps
  * in FP8); the MH correction evaluates log q of x and x' in one launch of
- * that kernel.  The proposal is drawn by a separate kernel (BF16: wavefront
- * sampler; FP8: sequential sampler) whose logits equal the scoring kernel's
- * up to the order of the fp32 sums.  Either precision therefore samples the
+ * that kernel.  The proposal is drawn by a separate kernel (a wavefront
+ * sampler, mma.sync BF16 or E4M3) whose logits equal the scoring kernel's up
+ * to the order of the fp32 sums.  Either precision therefore samples the
  * Boltzmann distribution up to a relative bias of about 1e-6 (and the 2^-32
  * quantization of the sampling thresholds); FP8 changes the acceptance rate
  * and the cost.  A bounded wait of the scoring kernel that runs out (1 s)

@@ -368,13 +368,11 @@ __device__ __forceinline__ void mma16816_bias(float (&d)[4], const uint32_t (&a)
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(c0), "f"(c1));
 }
 
-__global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_kernel(NetPtrs net, int8_t* win, int n, float* lq,
-                                                                  const LearnedKey* keys, uint32_t round_t) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    uint2* tabR = reinterpret_cast<uint2*>(smem + kWarpsSmp * kWinT * kSmpWinStride);
-    uint32_t* tabC = reinterpret_cast<uint32_t*>(smem + kWarpsSmp * kWinT * kSmpWinStride + kSmpTabR);
+// Per-step row tables of the wavefront samplers, filled by the whole block:
+// per (step, tile row) 8 bytes {source slot of taps 0..4, own slot (or
+// trash), draw index (0xFF: nothing to sample), padded site row}; per (step,
+// g) 4 bytes {padded site rows of tile rows g and g + 8, their own slots}.
+__device__ void fill_sampler_tables(uint2* tabR, uint32_t* tabC) {
     for (int i = threadIdx.x; i < kSteps * 16; i += blockDim.x) {
         const int st = i >> 4, row = i & 15, k = row % kPerStep;
         uint32_t b[8] = {kZeroSlot, kZeroSlot, kZeroSlot, kZeroSlot, kZeroSlot, kTrashSlot, 0xFFu, kRow0};
@@ -407,6 +405,16 @@ __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_kernel(NetPtrs ne
         }
         tabC[i] = v;
     }
+}
+
+__global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_kernel(NetPtrs net, int8_t* win, int n, float* lq,
+                                                                  const LearnedKey* keys, uint32_t round_t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    uint2* tabR = reinterpret_cast<uint2*>(smem + kWarpsSmp * kWinT * kSmpWinStride);
+    uint32_t* tabC = reinterpret_cast<uint32_t*>(smem + kWarpsSmp * kWinT * kSmpWinStride + kSmpTabR);
+    fill_sampler_tables(tabR, tabC);
     unsigned char* wb = smem + warp * kWinT * kSmpWinStride;
     auto wbase = [&](int w) -> unsigned char* { return wb + w * kSmpWinStride; };
     uint32_t bw1[2][2], bw2[5][2][2], bw3[5][2][2], bw4[2];
@@ -582,17 +590,10 @@ __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_kernel(NetPtrs ne
 }
 
 // ---------------------------------------------------------------------------
-// FP8 (E4M3) inference variant of the sequential forward: weights enter as
-// e4m3(W * s_l) with a per-layer power-of-two scale s_l, activations as
-// e4m3(relu(.)) (satfinite, round to nearest even), products summed in fp32
-// by mma.sync.m16n8k32 e4m3 x e4m3 -> f32 and divided by s_l.  K = 32 covers
-// two taps per k-step (taps 0+1, 2+3, 4+zero); layer 1's 16 features fill
-// the first half of one k-step.  Same window layout and outputs as the BF16
-// kernel (no activation output: inference only).
+// FP8 (E4M3) helpers: 16-byte activation rows, mma.sync.m16n8k32 e4m3 x e4m3 ->
+// f32, and B fragments from the e4m3 weight copy.
 // ---------------------------------------------------------------------------
-constexpr int kRowQ = 16;                                     // fp8 per activation row (conflict-free as is)
-constexpr int kRingQBytes = 3 * kSlots * kWin * kRowQ;        // 4608
-constexpr int kWarpSmemQ = kSpinBytes + kRingQBytes;          // 5408 (multiple of 16)
+constexpr int kRowQ = 16;                                     // fp8 per activation row (16 channels)
 
 __device__ __forceinline__ void mma16832_e4m3(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
@@ -600,12 +601,6 @@ __device__ __forceinline__ void mma16832_e4m3(float (&d)[4], const uint32_t (&a)
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t pack4_fp8(float a, float b, float c, float d) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return lo | (hi << 16);
 }
 
 // B fragment (K x N = 32 x 8, 8-bit) from the fp8 weight copy: k = 4*(lane%4)
@@ -623,175 +618,239 @@ __device__ __forceinline__ void load_b8(F wk, uint32_t (&b)[2]) {
     b[1] = r1;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kWarpsFwd * 32) ar_net_fp8_kernel(const uint8_t* wq, const float* wscale,
-                                                                     const float* wf, int8_t* win, int n, float* lq,
-                                                                     float* z_out, const LearnedKey* keys,
-                                                                     uint32_t round_t) {
+// ---------------------------------------------------------------------------
+// FP8 (E4M3) autoregressive sampling by wavefronts: the schedule, tables and
+// window grouping of ar_sample_kernel (28 steps of at most five positions,
+// three windows per warp, rows 5w + k of the m16 tile), with the FP8
+// arithmetic of the sequential FP8 kernel: e4m3 activations, e4m3 weights
+// times their power-of-two layer scale, mma.sync.m16n8k32 e4m3 x e4m3 -> f32.
+// One k32 step takes two taps: the four taps of the previous steps pair up as
+// (0, 1) and (2, 3), gathered by ldmatrix from per-window rings of 16-byte
+// rows (lanes 0-15 address the first tap's rows, lanes 16-31 the second's);
+// the (0, 0) tap is this step's own output, with a zero second half.  An
+// m16n8k32 accumulator fragment (channels 2tq, 2tq + 1 and 8 + 2tq, 9 + 2tq of
+// rows g, g + 8) is not the operand fragment the next layer needs (channels
+// 4tq .. 4tq + 3), so each layer's rounded output is regrouped by two warp
+// shuffles per row before its own-tap product and its stmatrix into the ring.
+// Accumulators start at bias x s_l (exact: s_l is a power of two) and are
+// scaled by 1 / s_l before relu and the e4m3 rounding, as (sum / s_l) + bias.
+// ---------------------------------------------------------------------------
+constexpr int kSmpQRing = 2 * kLayerRows * kRowQ;               // layers 1 and 2: 704 bytes
+constexpr int kSmpQSpin = kSmpQRing;                            // interior then ring spins, e4m3 codes
+constexpr int kSmpQU = kSmpQSpin + 2 * kSpinRows;               // u ring: kLayerRows x 5 floats (+2)
+constexpr int kSmpQDraws = kSmpQU + 112 * 4;                    // 64 draws
+constexpr int kSmpQWinBytes = kSmpQDraws + 64 * 4;              // 1680 = 105 16-byte chunks (odd)
+constexpr int kSmpQSmem = kWarpsSmp * kWinT * kSmpQWinBytes + kSmpTabR + kSmpTabC;
+static_assert(kSmpQU % 16 == 0 && kSmpQWinBytes % 16 == 0 && (kSmpQWinBytes / 16) % 2 == 1, "fp8 sampler layout");
+constexpr uint8_t kE4m3Plus = 0x38, kE4m3Minus = 0xB8;          // +1, -1
+
+__device__ __forceinline__ void stmatrix_x2(uint32_t addr, uint32_t r0, uint32_t r1) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x2.shared.b16 [%0], {%1, %2};\n" :: "r"(addr), "r"(r0), "r"(r1) : "memory");
+}
+
+// This lane's operand word (channels 4tq .. 4tq + 3 of a row) from the e4m3
+// pairs of the row's accumulator fragment across the lane's quad: p0 holds
+// channels (2tq, 2tq + 1), p1 channels (8 + 2tq, 9 + 2tq).
+__device__ __forceinline__ uint32_t regroup_e4m3(uint32_t p0, uint32_t p1, int lane) {
+    const uint32_t v = p0 | (p1 << 16);
+    const int tq = lane & 3, src = (lane & ~3) + 2 * (tq & 1), sh = (tq >> 1) * 16;
+    const uint32_t lo = __shfl_sync(0xffffffffu, v, src), hi = __shfl_sync(0xffffffffu, v, src + 1);
+    return ((lo >> sh) & 0xFFFFu) | (((hi >> sh) & 0xFFFFu) << 16);
+}
+
+// relu(d / s) rounded to e4m3 for the two n-tiles of a row pair, regrouped:
+// out[0] = row g, out[1] = row g + 8 (operand words of this lane)
+__device__ __forceinline__ void layer_out_e4m3(const float (&d)[2][4], float inv_s, int lane, uint32_t (&out)[2]) {
+    auto p = [&](float a, float b) -> uint32_t {
+        return __nv_cvt_float2_to_fp8x2(make_float2(fmaxf(a * inv_s, 0.0f), fmaxf(b * inv_s, 0.0f)), __NV_SATFINITE,
+                                        __NV_E4M3);
+    };
+    out[0] = regroup_e4m3(p(d[0][0], d[0][1]), p(d[1][0], d[1][1]), lane);
+    out[1] = regroup_e4m3(p(d[0][2], d[0][3]), p(d[1][2], d[1][3]), lane);
+}
+
+__global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_fp8_kernel(const uint8_t* wq, const float* wscale,
+                                                                       const float* wf, int8_t* win, int n, float* lq,
+                                                                       const LearnedKey* keys, uint32_t round_t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;
-    const int w0 = (blockIdx.x * kWarpsFwd + warp) * kWin;
-    if (w0 >= n) return;
-    int8_t* sp = reinterpret_cast<int8_t*>(smem + warp * kWarpSmemQ);
-    uint8_t* ring = smem + warp * kWarpSmemQ + kSpinBytes;
-    auto H = [&](int layer, int slot, int row) -> uint8_t* {
-        return ring + ((layer * kSlots + slot) * kWin + row) * kRowQ;
-    };
-    for (int i = lane; i < kWin * kNPos; i += 32) {
-        const int row = i / kNPos;
-        sp[i] = (w0 + row < n) ? win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] : (int8_t)0;
-    }
-    // B fragments: layer 1 (k = feature < 16), layers 2/3 (k-step s: taps 2s, 2s+1), layer 4 (N = 1)
-    uint32_t bq1[2][2], bq2[3][2][2], bq3[3][2][2], bq4[3][2];
+    uint2* tabR = reinterpret_cast<uint2*>(smem + kWarpsSmp * kWinT * kSmpQWinBytes);
+    uint32_t* tabC = reinterpret_cast<uint32_t*>(smem + kWarpsSmp * kWinT * kSmpQWinBytes + kSmpTabR);
+    fill_sampler_tables(tabR, tabC);
+    unsigned char* wb = smem + warp * kWinT * kSmpQWinBytes;
+    auto wbase = [&](int w) -> unsigned char* { return wb + w * kSmpQWinBytes; };
+    const float s1 = wscale[0], s2 = wscale[1], s3 = wscale[2];
+    const float inv_s[4] = {1.0f / wscale[0], 1.0f / wscale[1], 1.0f / wscale[2], 1.0f / wscale[3]};
+    // B fragments: layer 1 (features | zero), layers 2/3: (tap 0 | tap 1), (tap 2 | tap 3), (tap 4 | zero);
+    // layer 4: k = channel (| zero), n = tap
+    uint32_t bq1[2][2], bq2[3][2][2], bq3[3][2][2], bq4[2];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
         load_b8([&](int k, int nn) -> uint8_t { return k < 16 ? wq[kOffW1 + k * kC + nt * 8 + nn] : 0; }, bq1[nt]);
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
+        for (int pr = 0; pr < 3; ++pr) {
             load_b8([&](int k, int nn) -> uint8_t {
-                const int t = 2 * s + (k >> 4), ci = k & 15;
-                return t < 5 ? wq[kOffW2 + t * 256 + ci * kC + nt * 8 + nn] : 0;
-            }, bq2[s][nt]);
+                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = k & 15;
+                return t >= 0 ? wq[kOffW2 + t * 256 + ci * kC + nt * 8 + nn] : 0;
+            }, bq2[pr][nt]);
             load_b8([&](int k, int nn) -> uint8_t {
-                const int t = 2 * s + (k >> 4), ci = k & 15;
-                return t < 5 ? wq[kOffW3 + t * 256 + ci * kC + nt * 8 + nn] : 0;
-            }, bq3[s][nt]);
+                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = k & 15;
+                return t >= 0 ? wq[kOffW3 + t * 256 + ci * kC + nt * 8 + nn] : 0;
+            }, bq3[pr][nt]);
         }
     }
-#pragma unroll
-    for (int s = 0; s < 3; ++s)
-        load_b8([&](int k, int nn) -> uint8_t {
-            const int t = 2 * s + (k >> 4), ci = k & 15;
-            return (t < 5 && nn == 0) ? wq[kOffW4 + t * kC + ci] : 0;
-        }, bq4[s]);
-    const float inv_s[4] = {1.0f / wscale[0], 1.0f / wscale[1], 1.0f / wscale[2], 1.0f / wscale[3]};
-    float bias[3][2][2];
+    load_b8([&](int k, int nn) -> uint8_t { return (k < 16 && nn < 5) ? wq[kOffW4 + nn * kC + k] : 0; }, bq4);
+    float bias_s[3][2][2];                         // bias x s_l: the accumulators' start
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int co = nt * 8 + 2 * tq + e;
-            bias[0][nt][e] = wf[kOffB1 + co];
-            bias[1][nt][e] = wf[kOffB2 + co];
-            bias[2][nt][e] = wf[kOffB3 + co];
+            bias_s[0][nt][e] = wf[kOffB1 + co] * s1;
+            bias_s[1][nt][e] = wf[kOffB2 + co] * s2;
+            bias_s[2][nt][e] = wf[kOffB3 + co] * s3;
         }
     const float b4 = wf[kOffB4];
-    // this thread's four layer-1 features: k = 4tq .. 4tq+3
-    int fdy[4], fdx[4], fkind[4];
+    // this lane's four layer-1 features 4tq .. 4tq + 3: offsets into the window's
+    // spin codes (ring codes kSpinRows further) and whether the feature is zero
+    int foff[4];
+    bool fzero[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int k = 4 * tq + e;
-        fdy[e] = c_feat[k][0];
-        fdx[e] = c_feat[k][1];
-        fkind[e] = c_feat[k][2];
+        const int k = 4 * tq + e, kind = c_feat[k][2];
+        foff[e] = kind == 2 ? 0 : (kind == 1 ? kSpinRows : 0) + c_feat[k][0] * kPW + c_feat[k][1];
+        fzero[e] = kind == 2;
     }
-    float lq_acc = 0.0f;
-    __syncwarp();
+    const int lr = lane & 15, lwc = min(lr / kPerStep, kWinT - 1);
+    const int cw0 = g / kPerStep, cw1c = min((g + 8) / kPerStep, kWinT - 1);
+    const uint32_t ring_l = (uint32_t)__cvta_generic_to_shared(wbase(lwc));
+    const uint8_t* spin0 = wbase(cw0) + kSmpQSpin;
+    const uint8_t* spin1 = wbase(cw1c) + kSmpQSpin;
+    float* u0 = reinterpret_cast<float*>(wbase(cw0) + kSmpQU);
+    float* u1 = reinterpret_cast<float*>(wbase(cw1c) + kSmpQU);
+    unsigned char* wl = wbase(lwc);
+    const float* ul = reinterpret_cast<const float*>(wl + kSmpQU);
+    __syncthreads();
 
-    for (int p = 0; p < kNPos; ++p) {
-        const int r = p / kS, c = p - r * kS, slot = p % kSlots;
-        uint32_t a[4];
-        {
-            const int8_t* s = sp + g * kNPos;
-            float f[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int yy = r + fdy[e], xx = c + fdx[e];
-                float v = 0.0f;
-                if (fkind[e] != 2 && yy >= 0 && yy < kS && xx >= 0 && xx < kS) {
-                    const bool in = interior(yy, xx);
-                    if ((fkind[e] == 0) == in) v = (float)s[yy * kS + xx];
-                }
-                f[e] = v;
+    constexpr uint32_t kL2 = kLayerRows * kRowQ;         // the layer-2 ring after the layer-1 ring
+    for (int w0 = (blockIdx.x * kWarpsSmp + warp) * kWinT; w0 < n; w0 += gridDim.x * kWarpsSmp * kWinT) {
+        for (int i = lane; i < kWinT * kSmpQWinBytes / 4; i += 32) reinterpret_cast<uint32_t*>(wb)[i] = 0u;
+        __syncwarp();
+        for (int i = lane; i < kWinT * kNPos; i += 32) {
+            const int w = i / kNPos, p = i - w * kNPos;
+            if (w0 + w < n && !interior(p / kS, p % kS)) {
+                const int8_t x = win[(size_t)(w0 + w) * kNPos + p];
+                (wbase(w) + kSmpQSpin)[kSpinRows + padded_row(p)] = x > 0 ? kE4m3Plus : (x < 0 ? kE4m3Minus : 0);
             }
-            a[0] = pack4_fp8(f[0], f[1], f[2], f[3]);
-            a[1] = 0u;
-            a[2] = 0u;
-            a[3] = 0u;
         }
-#pragma unroll
-        for (int layer = 0; layer < 3; ++layer) {
-            float d[2][2][4] = {};
-            if (layer == 0) {
-                mma16832_e4m3(d[0][0], a, bq1[0]);
-                mma16832_e4m3(d[0][1], a, bq1[1]);
-            } else {
-#pragma unroll
-                for (int s = 0; s < 3; ++s) {
-                    uint32_t at[4] = {0u, 0u, 0u, 0u};
-                    bool any = false;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int t = 2 * s + h;
-                        if (t >= 5) continue;
-                        const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
-                        if (yy < 0 || xx < 0 || xx >= kS) continue;
-                        const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
-                        at[2 * h] = *reinterpret_cast<const uint32_t*>(H(layer - 1, sl, g) + 4 * tq);
-                        any = true;
-                    }
-                    if (!any) continue;
-                    if (layer == 1) { mma16832_e4m3(d[s & 1][0], at, bq2[s][0]); mma16832_e4m3(d[s & 1][1], at, bq2[s][1]); }
-                    else { mma16832_e4m3(d[s & 1][0], at, bq3[s][0]); mma16832_e4m3(d[s & 1][1], at, bq3[s][1]); }
-                }
-            }
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int co = nt * 8 + 2 * tq;
-                const float v0 = fmaxf((d[0][nt][0] + d[1][nt][0]) * inv_s[layer] + bias[layer][nt][0], 0.f);
-                const float v1 = fmaxf((d[0][nt][1] + d[1][nt][1]) * inv_s[layer] + bias[layer][nt][1], 0.f);
-                const unsigned short q = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
-                *reinterpret_cast<unsigned short*>(H(layer, slot, g) + co) = q;
-            }
-            __syncwarp();
-        }
-        float d4[2][4] = {};
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            uint32_t at[4] = {0u, 0u, 0u, 0u};
-            bool any = false;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = 2 * s + h;
-                if (t >= 5) continue;
-                const int yy = r + c_tapB[t][0], xx = c + c_tapB[t][1];
-                if (yy < 0 || xx < 0 || xx >= kS) continue;
-                const int sl = (p + c_tapB[t][0] * kS + c_tapB[t][1] + kSlots) % kSlots;
-                at[2 * h] = *reinterpret_cast<const uint32_t*>(H(2, sl, g) + 4 * tq);
-                any = true;
-            }
-            if (any) mma16832_e4m3(d4[s & 1], at, bq4[s]);
-        }
-        if (tq == 0) {
-            const int w = w0 + g;
-            const float z = (d4[0][0] + d4[1][0]) * inv_s[3] + b4;
-            if (w < n) {
-                if (z_out) z_out[(size_t)w * kNPos + p] = z;
-                if (interior(r, c)) {
-                    int8_t x = sp[g * kNPos + p];
-                    if (MODE == 1) {
-                        const LearnedKey k = keys[w];
-                        const int i = (r - 1) * kP + (c - 1);
-                        const uint4 rv = philox(16u * k.j + (uint32_t)(i >> 2), round_t, k.sim, 4u, k.key0, k.key1);
-                        const uint32_t u = (i & 3) == 0 ? rv.x : (i & 3) == 1 ? rv.y : (i & 3) == 2 ? rv.z : rv.w;
-                        const float sg = 1.0f / (1.0f + expf(-z));
-                        const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
-                        x = (u < thr) ? (int8_t)1 : (int8_t)-1;
-                        sp[g * kNPos + p] = x;
-                    }
-                    lq_acc += log_sigmoid((float)x * z);
-                }
+        for (int bq = lane; bq < kWinT * 16; bq += 32) {
+            const int w = bq >> 4, q = bq & 15;
+            if (w0 + w < n) {
+                const LearnedKey k = keys[w0 + w];
+                const uint4 rv = philox(16u * k.j + (uint32_t)q, round_t, k.sim, 4u, k.key0, k.key1);
+                uint32_t* d = reinterpret_cast<uint32_t*>(wbase(w) + kSmpQDraws) + 4 * q;
+                d[0] = rv.x; d[1] = rv.y; d[2] = rv.z; d[3] = rv.w;
             }
         }
         __syncwarp();
-    }
-    if (tq == 0 && w0 + g < n) lq[w0 + g] = lq_acc;
-    if (MODE == 1) {
-        for (int i = lane; i < kWin * kNPos; i += 32) {
-            const int row = i / kNPos;
-            if (w0 + row < n) win[(size_t)(w0 + row) * kNPos + (i - row * kNPos)] = sp[i];
+        float lq_acc = 0.0f;
+#pragma unroll 1
+        for (int s = 0; s < kSteps; ++s) {
+            const uint2 dr = tabR[s * 16 + lr];
+            const uint32_t dc = tabC[s * 8 + g];
+            const uint32_t sl0 = dr.x & 0xFF, sl1 = (dr.x >> 8) & 0xFF, sl2 = (dr.x >> 16) & 0xFF, sl3 = dr.x >> 24;
+            const uint32_t sl4 = dr.y & 0xFF, own = (dr.y >> 8) & 0xFF;
+            // ---- ring taps of layers 2 and 3 (pairs (0 | 1), (2 | 3)) into accumulators at bias x s ----
+            float d2[2][4], d3[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                d2[nt][0] = d2[nt][2] = bias_s[1][nt][0]; d2[nt][1] = d2[nt][3] = bias_s[1][nt][1];
+                d3[nt][0] = d3[nt][2] = bias_s[2][nt][0]; d3[nt][1] = d3[nt][3] = bias_s[2][nt][1];
+            }
+            {
+                const uint32_t pa = (lane < 16 ? sl0 : sl1) * kRowQ, pb = (lane < 16 ? sl2 : sl3) * kRowQ;
+                uint32_t at[4];
+                ldmatrix_x4(at, ring_l + pa);
+                mma16832_e4m3(d2[0], at, bq2[0][0]); mma16832_e4m3(d2[1], at, bq2[0][1]);
+                ldmatrix_x4(at, ring_l + pb);
+                mma16832_e4m3(d2[0], at, bq2[1][0]); mma16832_e4m3(d2[1], at, bq2[1][1]);
+                ldmatrix_x4(at, ring_l + kL2 + pa);
+                mma16832_e4m3(d3[0], at, bq3[0][0]); mma16832_e4m3(d3[1], at, bq3[0][1]);
+                ldmatrix_x4(at, ring_l + kL2 + pb);
+                mma16832_e4m3(d3[0], at, bq3[1][0]); mma16832_e4m3(d3[1], at, bq3[1][1]);
+            }
+            // ---- layer 1: features 4tq .. 4tq + 3 of rows g, g + 8 ----
+            const int q0 = dc & 0xFF, q1 = (dc >> 8) & 0xFF;
+            uint32_t h[2];
+            {
+                uint32_t f0 = 0, f1 = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (fzero[e]) continue;
+                    f0 |= (uint32_t)spin0[q0 + foff[e]] << (8 * e);
+                    f1 |= (uint32_t)spin1[q1 + foff[e]] << (8 * e);
+                }
+                const uint32_t a[4] = {f0, f1, 0u, 0u};
+                float d[2][4];
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    d[nt][0] = d[nt][2] = bias_s[0][nt][0]; d[nt][1] = d[nt][3] = bias_s[0][nt][1];
+                    mma16832_e4m3(d[nt], a, bq1[nt]);
+                }
+                layer_out_e4m3(d, inv_s[0], lane, h);
+                stmatrix_x2(ring_l + own * kRowQ, h[0], h[1]);
+            }
+            // ---- layers 2 and 3: the (0, 0) taps ----
+            {
+                const uint32_t a[4] = {h[0], h[1], 0u, 0u};
+                mma16832_e4m3(d2[0], a, bq2[2][0]); mma16832_e4m3(d2[1], a, bq2[2][1]);
+            }
+            layer_out_e4m3(d2, inv_s[1], lane, h);
+            stmatrix_x2(ring_l + kL2 + own * kRowQ, h[0], h[1]);
+            {
+                const uint32_t a[4] = {h[0], h[1], 0u, 0u};
+                mma16832_e4m3(d3[0], a, bq3[2][0]); mma16832_e4m3(d3[1], a, bq3[2][1]);
+            }
+            layer_out_e4m3(d3, inv_s[2], lane, h);
+            // ---- layer 4: u[t] (unscaled) of rows g, g + 8 into the u ring ----
+            {
+                const uint32_t a[4] = {h[0], h[1], 0u, 0u};
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+                mma16832_e4m3(d4, a, bq4);
+                const int c0 = 2 * tq, o0 = (int)((dc >> 16) & 0xFF) * 5 + c0, o1 = (int)(dc >> 24) * 5 + c0;
+                if (c0 < 5) { u0[o0] = d4[0]; u1[o1] = d4[2]; }
+                if (c0 + 1 < 5) { u0[o0 + 1] = d4[1]; u1[o1 + 1] = d4[3]; }
+            }
+            __syncwarp();
+            // ---- sample: lane lr < 15 takes its row's site when it has one ----
+            const uint32_t di = (dr.y >> 16) & 0xFF;
+            if (lane < 16 && di != 0xFFu) {
+                const float z = (ul[sl0 * 5 + 0] + ul[sl1 * 5 + 1] + ul[sl2 * 5 + 2] + ul[sl3 * 5 + 3] + ul[sl4 * 5 + 4]) *
+                                    inv_s[3] + b4;
+                const uint32_t draw = reinterpret_cast<const uint32_t*>(wl + kSmpQDraws)[di];
+                const float sg = __frcp_rn(1.0f + expf(-z));
+                const uint32_t thr = (sg >= 1.0f) ? 0xFFFFFFFFu : (uint32_t)(sg * 4294967296.0f);
+                const float x = draw < thr ? 1.0f : -1.0f;
+                (wl + kSmpQSpin)[dr.y >> 24] = x > 0.f ? kE4m3Plus : kE4m3Minus;
+                if (lq) lq_acc += log_sigmoid(x * z);
+            }
+            __syncwarp();
         }
+        float* lqs = reinterpret_cast<float*>(wb + kSmpQU);
+        if (lane < 16) lqs[lane] = lq_acc;
+        __syncwarp();
+        if (lane < kWinT && w0 + lane < n && lq) {
+            float t = 0.0f;
+            for (int k = 0; k < kPerStep; ++k) t += lqs[kPerStep * lane + k];
+            lq[w0 + lane] = t;
+        }
+        for (int i = lane; i < kWinT * kNPos; i += 32) {
+            const int w = i / kNPos, p = i - w * kNPos;
+            if (w0 + w < n && interior(p / kS, p % kS))
+                win[(size_t)(w0 + w) * kNPos + p] = (wbase(w) + kSmpQSpin)[padded_row(p)] == kE4m3Plus ? (int8_t)1 : (int8_t)-1;
+        }
+        __syncwarp();
     }
 }
 
@@ -1129,6 +1188,8 @@ cudaError_t configure_learned_kernels() {
                                          kWarpsFwd * kWarpSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ar_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ar_sample_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmpQSmem);
     const int bwd = (((kNParams + 3) / 4) * 4 + kWarpsBwd * 2 * kNPos * kC) * (int)sizeof(float);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(net_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd);
@@ -1146,8 +1207,9 @@ cudaError_t launch_net_forward(const NetState& ns, const int8_t* win, int n, flo
 cudaError_t launch_net_sample_fp8(const NetState& ns, int8_t* win, int n, float* lq, const LearnedKey* keys,
                                   uint32_t round_t, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
-    ar_net_fp8_kernel<1><<<fwd_blocks(n), kWarpsFwd * 32, kWarpsFwd * kWarpSmemQ, stream>>>(
-        ns.wq, ns.wscale, ns.w, win, n, lq, nullptr, keys, round_t);
+    const int blocks = std::min((n + kWarpsSmp * kWinT - 1) / (kWarpsSmp * kWinT), device_sm_count() * 4);
+    ar_sample_fp8_kernel<<<blocks, kWarpsSmp * 32, kSmpQSmem, stream>>>(ns.wq, ns.wscale, ns.w, win, n, lq, keys,
+                                                                       round_t);
     return cudaGetLastError();
 }
 

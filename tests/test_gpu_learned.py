@@ -116,6 +116,36 @@ def test_sample_matches_oracle_except_near_ties():
     assert mism <= 2
 
 
+@pytest.mark.parametrize("B", [40, 4000])
+def test_fp8_sample_matches_oracle_except_near_ties(B):
+    """The FP8 wavefront sampler (e4m3 activations and weights, two taps per
+    k32 step) against the oracle's FP8 sampler: identical interiors except at
+    a site whose draw lies within 1 % of its threshold (the fp32 sums of the
+    two differ in order); 4,000 windows: several window triples per warp."""
+    net = ising.IsingNet(max_windows=B)
+    flat = ol.init_params(13, gain=1.5)
+    net.set_params(flat)
+    net.set_precision(ising.ISING_NET_FP8)
+    win = rand_windows(B, 3)
+    seed, s, rnd = 0xABCDEF12345, 7, 3
+    keys = np.array([[seed & 0xFFFFFFFF, seed >> 32, s, j] for j in range(B)], np.uint32)
+    gw, glq = net.sample(win, keys, rnd)
+    pick = list(range(B)) if B <= 40 else sorted(np.random.default_rng(4).choice(B - 60, 60, replace=False).tolist()) + \
+        list(range(B - 60, B))
+    R = np.stack([ol.sampling_draws(seed, s, j, rnd) for j in pick])
+    ow, olq, thr = ol.sample(win[pick], flat, R, prec="fp8")
+    mism = 0
+    for i, j in enumerate(pick):
+        assert np.array_equal(gw[j].reshape(10, 10)[0], win[j][0])          # ring untouched
+        k = _first_diff(gw[j].reshape(10, 10), ow[i])
+        if k < 0:
+            assert abs(glq[j] - olq[i]) < 5e-2
+            continue
+        mism += 1
+        assert abs(R[i, k] - thr[i, k]) < 1e-2 * 2**32, (j, k, R[i, k], thr[i, k])   # a near-tie
+    assert mism <= max(2, len(pick) // 20)
+
+
 def test_sample_large_batch_matches_oracle_on_a_subset():
     """8,000 windows: more window triples than the persistent sampler has
     warps (4 blocks of 4 warps per SM), so some warps take a second triple;
