@@ -31,7 +31,6 @@ T_RUNS = (1.5, 2.269185, 3.0)
 # algorithmic integer ops per site update: a quarter Philox4x32-10 block (15),
 # the accept decision (3), the bitsliced neighbour count (0.5)
 OPS_PER_SITE = 18.5
-SMS = 152
 SINGLE_THREAD_L = 4096   # lattice of the single-thread oracle figure
 # the paper's own figures, for context only (other hardware and workloads)
 PAPER_CONTEXT = {
@@ -40,8 +39,9 @@ PAPER_CONTEXT = {
                  "459 on one V100",
     "note": "other hardware and workloads: context, not a target",
 }
-INT_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# 32-bit integer lanes per SM of compute capability 10.x (Blackwell); the
+# device query below supplies the SM count and the maximum SM clock
+INT_LANES_PER_SM = {(10, 0): 128, (10, 3): 128}
 # (workload, kernel, sites per launch) -> dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch of that kernel build, from an ncu full
 # capture (first captured launch); other pairings report null
@@ -155,6 +155,27 @@ class ClockSampler:
                     "note": self.err or "no nvidia-smi samples"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def device_figures(dev, uuid: str | None) -> dict:
+    """SM count and compute capability from the device, the maximum SM clock
+    from nvidia-smi (the GPU's own report; 2070 MHz, the GB300 maximum, if
+    nvidia-smi is unavailable)."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    cc = (p.major, p.minor)
+    mhz, src = 2070.0, "GB300 maximum (nvidia-smi unavailable)"
+    try:
+        cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
+        if uuid:
+            cmd += ["-i", uuid]
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        if out:
+            mhz, src = float(out[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    return {"sms": p.multi_processor_count, "cc": cc, "int_lanes_per_sm": INT_LANES_PER_SM.get(cc, 128),
+            "sm_max_mhz": mhz, "clock_source": src}
 
 
 def workload_sweeps(args) -> int:
@@ -417,7 +438,8 @@ def ours(args):
     avg_launch_s = (sum(step_ms) / 1e3) / n_launch
     sites_per_launch = flips_per_step * args.steps / n_launch
     achieved = OPS_PER_SITE * sites_per_launch / avg_launch_s / 1e12
-    peak = SMS * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    devf = device_figures(dev, uuid)
+    peak = devf["sms"] * devf["int_lanes_per_sm"] * devf["sm_max_mhz"] * 1e6 / 1e12
     # DRAM bytes (read + write) per launch from the ncu capture of this kernel
     # on this workload; null for any other kernel / workload pairing
     traffic = None
@@ -474,7 +496,9 @@ def ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": kname, "ops_per_site": OPS_PER_SITE,
-                         "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz"},
+                         "peak_basis": f"{devf['sms']} SMs x {devf['int_lanes_per_sm']} int32 lanes x "
+                                       f"{devf['sm_max_mhz']:.0f} MHz ({devf['clock_source']}; SM count from the "
+                                       f"device)"},
             "cpu_baseline": cpu,
             "learned_vs_plain": learned,
             "e2e": e2e,

@@ -243,7 +243,7 @@ def main():
     ap.add_argument("--fp8", action="store_true", help="with --round-bench: FP8 inference")
     args = ap.parse_args()
     if args.round_bench:
-        round_bench(args.round_bench, precision=1 if args.fp8 else 0)
+        round_bench(args.round_bench, L=args.L, replicas=args.replicas, precision=1 if args.fp8 else 0)
         return
     out = [run_temperature(T, L=args.L, replicas=args.replicas, burn=args.burn, n_snap=args.snapshots,
                            train_steps=args.train_steps, units=args.units) for T in args.temps]
