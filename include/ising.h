@@ -241,12 +241,23 @@ int ising_load(ising_t h, const void* host_buf, size_t bytes);
 /* ISING_PLAN_MIXED: lattices with L <= 1024 resident (as RESIDENT, grouped by
  * size), larger ones streamed (as STREAM), in the same sweeps. */
 #define ISING_PLAN_MIXED 4
+/* ISING_PLAN_CLUSTER: every lattice (L <= ISING_CLUSTER_MAX_L, else
+ * ISING_EINVAL) is held by one thread-block cluster of C CTAs for all sweeps
+ * of a call, CTA r owning rows [r L/C, (r+1) L/C) of both colours in shared
+ * memory; a half-sweep reads the rows next to its strip from the neighbouring
+ * CTAs' shared memory (distributed shared memory) and a cluster barrier
+ * separates the half-sweeps.  C is the largest power of two <= min(8,
+ * L / rows_per_item) (rows_per_item 0 = 64).  One launch per distinct L, all
+ * lattices of that size in it, then one to advance the sweep counter. */
+#define ISING_PLAN_CLUSTER 5
+#define ISING_CLUSTER_MAX_L 1024
 int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int sweeps_per_unit, int threads);
 
 /* Autotuner: time candidate plans (resident with sweeps_per_unit in {8, 32,
  * 128} and block sizes {auto, 256, 512} when some lattice has L <= 1024 --
- * RESIDENT if every lattice has, else MIXED;
+ * RESIDENT if every lattice has, else MIXED; CLUSTER with rows_per_item in
+ * {32, 64, 128} when every lattice has L <= 1024;
  * streaming with words_per_thread in {1, 2, 4}, rows_per_item in {1, 2, 4, 8},
  * threads in {128, 256}, and the persistent streaming kernel with the same
  * tilings) for probe_sweeps sweeps each on the handle's stream

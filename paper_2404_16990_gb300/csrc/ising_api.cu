@@ -134,6 +134,9 @@ struct ising_handle {
     size_t group_smem = 0;
     int res_threads = 0;
     int res_grid = 0;
+    // CLUSTER plan: classes of equal L, one thread-block cluster per lattice
+    struct ClusterClass { uint32_t L; int cluster; int member_off; int count; };
+    std::vector<ClusterClass> cl_classes;
     int n_slats = 0;
     uint64_t total_tiles = 0;
     int V = 1;                  // streaming tiling in use: words per thread and row,
@@ -176,6 +179,37 @@ int build_tables(ising_handle* h) {
     const size_t optin = device_max_smem_optin();
     const size_t static_smem = 16 * 1024;  // SiteKey/lattice tables and counters of the kernel
     const size_t res_budget = optin > static_smem ? optin - static_smem : 0;
+    h->cl_classes.clear();
+    if (h->plan.mode == ISING_PLAN_CLUSTER) {
+        // one thread-block cluster per lattice: C CTAs of rows_per_item rows
+        // (default 64), C the largest power of two <= min(8, L / rows)
+        const int rows = h->plan.rows_per_item > 0 ? h->plan.rows_per_item : 64;
+        std::map<int, std::vector<uint32_t>> by_L;
+        for (int i = 0; i < n; ++i) {
+            if (h->L[i] > ISING_CLUSTER_MAX_L)
+                return fail(ISING_EINVAL, "cluster plan: lattice %d has L=%d > %d", i, h->L[i], ISING_CLUSTER_MAX_L);
+            by_L[h->L[i]].push_back((uint32_t)i);
+        }
+        std::vector<uint32_t> members;
+        for (auto& kv : by_L) {
+            int c = 1;
+            while (c * 2 <= 8 && c * 2 <= std::max(1, kv.first / rows)) c *= 2;
+            h->cl_classes.push_back({(uint32_t)kv.first, c, (int)members.size(), (int)kv.second.size()});
+            members.insert(members.end(), kv.second.begin(), kv.second.end());
+        }
+        h->n_groups = 0;
+        h->n_slats = 0;
+        h->total_tiles = 0;
+        h->V = 1;
+        h->R = rows;
+        if (!members.empty())
+            CUDA_TRY(cudaMemcpyAsync(h->ws + h->layout.members, members.data(), members.size() * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, h->stream), "upload cluster members");
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize after table upload");
+        h->tables_ready = true;
+        drop_graphs(h);
+        return ISING_OK;
+    }
     std::vector<int> resident, streamed;
     for (int i = 0; i < n; ++i) {
         const size_t bytes = (size_t)h->L[i] * h->L[i] / 8;
@@ -351,6 +385,7 @@ int build_tables(ising_handle* h) {
 
 // Kernels one enqueue_sweeps(h, n) issues.
 int64_t kernels_per_call(const ising_handle* h, int64_t n) {
+    if (h->plan.mode == ISING_PLAN_CLUSTER) return (int64_t)h->cl_classes.size() + 1;
     int64_t k = 0;
     if (h->n_groups > 0) k += 1;
     if (h->n_slats > 0 && h->plan.mode == ISING_PLAN_PERSIST) k += 1;
@@ -360,6 +395,14 @@ int64_t kernels_per_call(const ising_handle* h, int64_t n) {
 }
 
 int enqueue_sweeps(ising_handle* h, int64_t n) {
+    if (h->plan.mode == ISING_PLAN_CLUSTER) {
+        const uint32_t* members = (const uint32_t*)(h->ws + h->layout.members);
+        for (const auto& c : h->cl_classes)
+            CUDA_TRY(launch_cluster_resident(h->st, members + c.member_off, c.count, c.cluster, c.L, n, h->stream),
+                     "cluster-resident kernel launch");
+        CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
+        return ISING_OK;
+    }
     if (h->n_groups > 0) {
         CUDA_TRY(cudaMemsetAsync(&h->st.ctl->ticket, 0, sizeof(unsigned int), h->stream), "reset tickets");
         CUDA_TRY(cudaMemsetAsync(h->st.done, 0, (size_t)h->n_groups * sizeof(unsigned int), h->stream),
@@ -803,7 +846,7 @@ int ising_set_plan(ising_t h, int plan, int words_per_thread, int rows_per_item,
                    int threads) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (plan != ISING_PLAN_AUTO && plan != ISING_PLAN_RESIDENT && plan != ISING_PLAN_STREAM &&
-        plan != ISING_PLAN_PERSIST && plan != ISING_PLAN_MIXED)
+        plan != ISING_PLAN_PERSIST && plan != ISING_PLAN_MIXED && plan != ISING_PLAN_CLUSTER)
         return fail(ISING_EINVAL, "unknown plan %d", plan);
     if (words_per_thread != 0 && words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4)
         return fail(ISING_EINVAL, "words_per_thread must be 0, 1, 2 or 4");
@@ -912,6 +955,8 @@ int ising_autotune(ising_t h, int64_t probe_sweeps, int force, double* best_flip
         for (int k : {8, 32, 128})
             for (int thr : {0, 256, 512})
                 cands.push_back({all_small ? ISING_PLAN_RESIDENT : ISING_PLAN_MIXED, 0, 0, k, thr});
+    if (all_small)
+        for (int rows : {32, 64, 128}) cands.push_back({ISING_PLAN_CLUSTER, 0, rows, 0, 0});
     const int Vs[] = {1, 2, 4};
     for (int V : Vs) {
         bool ok = true;
@@ -978,7 +1023,7 @@ int ising_get_plan(ising_t h, int* plan, int* words_per_thread, int* rows_per_it
     if (threads)
         *threads = (h->plan.mode == ISING_PLAN_STREAM || h->plan.mode == ISING_PLAN_PERSIST ||
                     h->plan.mode == ISING_PLAN_AUTO) ? h->plan.stream_threads
-                                                                                             : h->res_threads;
+                   : h->plan.mode == ISING_PLAN_CLUSTER ? 256 : h->res_threads;
     return ISING_OK;
 }
 

@@ -137,6 +137,10 @@ cudaError_t launch_stream_persistent(const DevState& st, int n_slats, uint64_t t
                                      int words_per_thread, int threads, int grid, int64_t n_sweeps,
                                      cudaStream_t stream);
 int stream_persistent_occupancy(int words_per_thread, int threads);
+// One thread-block cluster of cluster_size CTAs per lattice (members[0 ..
+// count)), all of side L, all n_sweeps sweeps in one launch.
+cudaError_t launch_cluster_resident(const DevState& st, const uint32_t* members, int count, int cluster_size,
+                                    uint32_t L, int64_t n_sweeps, cudaStream_t stream);
 cudaError_t launch_advance_t(const DevState& st, int64_t n, cudaStream_t stream);
 cudaError_t launch_random_stream(uint32_t k0, uint32_t k1, uint32_t s, uint32_t phase, uint64_t p0, uint64_t n_p,
                                  uint32_t t0, uint32_t n_t, uint32_t* out, cudaStream_t stream);

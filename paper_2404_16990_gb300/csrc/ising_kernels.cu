@@ -18,6 +18,7 @@
 #include "ising_internal.h"
 #include "ising_device.cuh"
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cstdint>
@@ -554,6 +555,86 @@ __global__ void __launch_bounds__(256, 2) stream_persist_kernel(DevState st, int
     if (blockIdx.x == 0 && threadIdx.x == 0) st.ctl->t = t0 + (unsigned long long)n_sweeps;
 }
 
+// ---------------------------------------------------------------------------
+// Cluster-resident kernel for small lattices: one thread-block cluster of C
+// CTAs per lattice, CTA rank r holding rows [r L/C, (r+1) L/C) of both colours
+// in shared memory for all sweeps of the call.  A half-sweep reads the rows
+// just above and below the strip straight from the neighbouring CTAs' shared
+// memory (distributed shared memory), and a cluster barrier separates the
+// half-sweeps -- the paper's halo refresh between the two colours
+// (Algorithm 6) without any copy.  E/M partial sums go to rank 0 by DSMEM
+// atomics; rank 0 records them after each sweep.  Lattice li of the class is
+// handled by cluster li (blockIdx.x / C); every lattice's L / C rows form
+// whole rows of words.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) cluster_resident_kernel(DevState st, const uint32_t* members, int count,
+                                                               long long n_sweeps) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ unsigned long long s_acc[2];          // rank 0: the cluster's E/M partial sums of a sweep
+    __shared__ unsigned long long red[64];
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t C = cluster.num_blocks(), r = cluster.block_rank();
+    const int li = (int)(blockIdx.x / C);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (li >= count) return;                          // whole clusters only (grid = count x C)
+    const uint32_t lat = members[li];
+    const LatDesc d = st.lat[lat];
+    const uint32_t L = d.L, wn = d.wn, rows = L / C, y0 = r * rows;
+    const uint32_t strip = rows * wn;                 // words of one colour in this CTA
+    uint32_t* base = st.spins + d.word_off;
+    for (uint32_t i = tid; i < 2 * strip; i += nthr) {
+        const uint32_t c = i / strip, j = i - c * strip;
+        sm[i] = __ldcg(base + ((size_t)c * L + y0) * wn + j);
+    }
+    if (tid < 2) s_acc[tid] = 0ull;
+    const unsigned long long t0 = st.ctl->t;
+    cluster.sync();                                   // every strip loaded
+    const uint32_t* up_sm = cluster.map_shared_rank(sm, (r + C - 1) % C);   // its last row is row y0 - 1
+    const uint32_t* dn_sm = cluster.map_shared_rank(sm, (r + 1) % C);       // its first row is row y0 + rows
+    unsigned long long* acc0 = cluster.map_shared_rank(s_acc, 0u);
+    for (long long it = 0; it < n_sweeps; ++it) {
+        const unsigned long long t = t0 + (unsigned long long)it;
+        for (uint32_t c = 0; c < 2; ++c) {
+            const uint32_t* opp = sm + (1u - c) * strip;
+            uint32_t* own = sm + c * strip;
+            const SiteKey key{(uint32_t)t, d.sim, c, d.key0, d.key1, d.thr0, d.thr1};
+            unsigned long long sa = 0, sp = 0;
+            for (uint32_t i = tid; i < strip; i += nthr) {
+                const uint32_t ly = i / wn, k = i - ly * wn, y = y0 + ly;
+                const uint32_t up = ly > 0 ? opp[i - wn] : up_sm[(1u - c) * strip + (rows - 1) * wn + k];
+                const uint32_t dn = ly + 1 < rows ? opp[i + wn] : dn_sm[(1u - c) * strip + k];
+                const uint32_t same = opp[i];
+                const bool plus = ((c ^ (y & 1u)) != 0);
+                const uint32_t kk = plus ? ((k + 1 == wn) ? 0 : k + 1) : ((k == 0) ? wn - 1 : k - 1);
+                const uint32_t side = side_word(plus, same, opp[ly * wn + kk]);
+                const uint32_t q0 = (y * (L >> 1) + 32u * k) >> 2;
+                const uint32_t w = metropolis_word(own[i], up, dn, same, side, q0, key);
+                own[i] = w;
+                if (c == 1) observe_word(w, up, dn, same, side, sa, sp);
+            }
+            if (c == 1) {
+                block_sum2(sa, sp, red);
+                if (tid == 0) {
+                    atomicAdd(&acc0[0], sa);
+                    atomicAdd(&acc0[1], sp);
+                }
+            }
+            cluster.sync();                           // this colour complete everywhere before the other is read
+            if (c == 1 && r == 0 && tid == 0) {
+                record(st, lat, L, s_acc[0], s_acc[1], t);
+                s_acc[0] = 0ull;                      // the next additions come after the next barrier
+                s_acc[1] = 0ull;
+            }
+        }
+    }
+    for (uint32_t i = tid; i < 2 * strip; i += nthr) {
+        const uint32_t c = i / strip, j = i - c * strip;
+        __stcg(base + ((size_t)c * L + y0) * wn + j, sm[i]);
+    }
+    cluster.sync();                                   // no CTA leaves while another may still read its memory
+}
+
 __global__ void advance_t_kernel(DevState st, long long n) { st.ctl->t += (unsigned long long)n; }
 
 // The draws of sites p0 .. p0 + n_p - 1 in sweeps t0 .. t0 + n_t - 1, one
@@ -727,6 +808,26 @@ cudaError_t launch_random_stream(uint32_t k0, uint32_t k1, uint32_t s, uint32_t 
     random_stream_kernel<<<(unsigned)grid, 256, 0, stream>>>(k0, k1, s, phase, (unsigned long long)p0,
                                                              (unsigned long long)n_p, t0, n_t,
                                                              (unsigned long long)blocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_resident(const DevState& st, const uint32_t* members, int count, int cluster_size,
+                                    uint32_t L, int64_t n_sweeps, cudaStream_t stream) {
+    if (count <= 0 || n_sweeps <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(count * cluster_size));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)L * L / 8 / (size_t)cluster_size;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster_size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_resident_kernel, st, members, count, (long long)n_sweeps);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

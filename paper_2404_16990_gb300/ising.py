@@ -32,6 +32,8 @@ ISING_PLAN_RESIDENT = 1
 ISING_PLAN_STREAM = 2
 ISING_PLAN_PERSIST = 3
 ISING_PLAN_MIXED = 4
+ISING_PLAN_CLUSTER = 5
+ISING_CLUSTER_MAX_L = 1024
 ISING_MIN_L = 64
 ISING_MAX_L = 65536
 
