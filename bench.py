@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--L", type=int, default=16384)
     ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754)")
     ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
-    ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream", "persist"], default="tuned",
+    ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream", "persist", "cluster"],
+                    default="tuned",
                     help="batch754: force a plan instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -377,7 +378,8 @@ def ours(args):
             sims.append(s)
     if args.workload == "batch754" and args.plan != "tuned":
         code = {"auto": ising.ISING_PLAN_AUTO, "resident": ising.ISING_PLAN_RESIDENT,
-                "stream": ising.ISING_PLAN_STREAM, "persist": ising.ISING_PLAN_PERSIST}[args.plan]
+                "stream": ising.ISING_PLAN_STREAM, "persist": ising.ISING_PLAN_PERSIST,
+                "cluster": ising.ISING_PLAN_CLUSTER}[args.plan]
         for s in sims:
             s.set_plan(code)
     for s in sims:
@@ -425,12 +427,16 @@ def ours(args):
 
     # dominant kernel, from the plan in use: streaming half-sweeps (two
     # launches per sweep per handle), the cooperative persistent streaming
-    # kernel or the resident kernel (one launch per sweep call per handle);
+    # kernel or the resident kernel (one launch per sweep call per handle),
+    # the cluster-resident kernel (one launch per lattice side per sweep call);
     # either way the algorithmic ops of the timed region over its duration
     plan = ising.ising_get_plan(sims[0].h)
     V = plan["words_per_thread"]
     if plan["plan"] == ising.ISING_PLAN_RESIDENT:
         kname, n_launch = "resident_kernel", len(sims) * args.steps
+    elif plan["plan"] == ising.ISING_PLAN_CLUSTER:
+        sides = [len({int(ising.ising_lattice_size(s.h, i)) for i in range(s.n)}) for s in sims]
+        kname, n_launch = "cluster_resident_kernel", sum(sides) * args.steps
     elif plan["plan"] == ising.ISING_PLAN_PERSIST:
         kname, n_launch = f"stream_persist_kernel<{V}>", len(sims) * args.steps
     else:
