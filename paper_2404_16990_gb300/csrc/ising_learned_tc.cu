@@ -22,10 +22,14 @@
 // descriptor's leading-dimension stride is the offset between the taps).
 //
 // Each layer: one thread issues the layer's MMAs for all windows of the chunk
-// and commits them to an mbarrier; every thread then reads its row (32x32b
-// tcgen05.ld: warp w reads lanes 32 (w % 4) ..), adds the bias, applies relu,
-// rounds to the layer's activation type (pad rows give zeros) and writes the
-// row back over the layer's input (all MMAs that read it have completed).
+// (per window BF16: 1 + 5 + 5 + 1, the layer-1 bias riding in W1's unused K
+// rows against features that are 1.0 there; E4M3: 1 + 3 + 3 + 1) and commits
+// them to an mbarrier; every thread then reads its row (32x32b tcgen05.ld:
+// warp w reads lanes 32 (w % 4) ..), adds the bias, applies relu and rounds
+// to the layer's activation type in one conversion (pad rows give zeros) and
+// writes the row back over the layer's input (all MMAs that read it have
+// completed).  With N = 16 an MMA does 16 FLOP per byte of A it reads from
+// shared memory, so the MMAs per window, not the tensor pipe, set the pace.
 // Same masks, weights, rounding points and fp32 accumulation as the other net
 // kernels; only the order of the fp32 sums differs.
 #include "../../include/ising.h"
@@ -65,19 +69,19 @@ template <bool FP8>
 struct TcLayout {
     static constexpr int kPlanes = FP8 ? 1 : 2;
     static constexpr int kAct = kPlanes * kTcPlane > kTcURows * 4 ? kPlanes * kTcPlane : kTcURows * 4;
-    // B tiles of 512 bytes; BF16 adds three bias tiles (the fp32 bias as three
-    // exact bf16 parts, k = 0, 1, 2) multiplied by the ones plane
-    static constexpr int kNTiles = FP8 ? 8 : 15;
+    // B tiles of 512 bytes.  BF16: W1 (its rows k = 13, 14, 15 hold the layer-1
+    // bias as three exact bf16 parts, met by features that are 1.0 there), the
+    // five taps of W2 and of W3, W4; E4M3: see the weight set-up below.
+    static constexpr int kNTiles = FP8 ? 8 : 12;
     static constexpr int kWts = kNTiles * 512;
     static constexpr int kOffWts = kAct;
-    static constexpr int kOffOnes = kOffWts + kWts;           // BF16: 128 rows x 16 B, 1.0 at k < 3 of real rows
-    static constexpr int kOffBias = kOffOnes + (FP8 ? 0 : kTcRows * 16);   // 3 x 16 fp32
+    static constexpr int kOffBias = kOffWts + kWts;           // 3 x 16 fp32
     // spins as operand codes (bf16 bits / e4m3 bytes): [window][interior, ring][kTcSpin]
     using SpinT = typename std::conditional<FP8, uint8_t, uint16_t>::type;
     static constexpr int kOffSpin = kOffBias + 3 * 16 * 4;
     static constexpr int kOffBar = kOffSpin + ((kTcWin * 2 * kTcSpin * (int)sizeof(SpinT) + 15) / 16) * 16;
     static constexpr int kBytes = kOffBar + 16;
-    static_assert(kOffWts % 128 == 0 && kOffOnes % 128 == 0 && kOffSpin % 16 == 0 && kOffBar % 8 == 0, "alignment");
+    static_assert(kOffWts % 128 == 0 && kOffSpin % 16 == 0 && kOffBar % 8 == 0, "alignment");
     static_assert(kBytes < (1 << 18), "descriptor address range");
 };
 
@@ -152,10 +156,12 @@ __device__ __forceinline__ bool tc_pad_row(int q) { return q < kPW + 1 || q >= 1
 
 __device__ __forceinline__ float tc_log_sigmoid(float t) { return -(fmaxf(-t, 0.0f) + log1pf(expf(-fabsf(t)))); }
 
-__device__ __forceinline__ uint32_t tc_pack_e4m3(float a, float b, float c, float d) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return lo | (hi << 16);
+// relu, then round to e4m3 (satfinite), a in the lowest byte: one conversion per pair
+__device__ __forceinline__ uint32_t tc_pack_e4m3_relu(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
 // The 16 layer-1 features: k < 4 interior spins at the mask-A taps, 4 <= k < 13
@@ -204,28 +210,24 @@ __global__ void __launch_bounds__(kTcThreads, 4) ar_score_tc_kernel(const TcArgs
     if constexpr (!FP8) {
         // tile = [2 chunks][16 n][8 k] bf16: element (n, k) at (k / 8) * 256 + n * 16 + (k % 8) * 2
         __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(wts);
-        for (int i = tid; i < 15 * 256; i += kTcThreads) {
+        for (int i = tid; i < Lay::kNTiles * 256; i += kTcThreads) {
             const int tile = i >> 8, n = (i >> 4) & 15, k = i & 15;
             __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (tile == 0) v = args.wb[kOffW1 + k * kC + n];
+            if (tile == 0) {
+                if (k < 13) {
+                    v = args.wb[kOffW1 + k * kC + n];
+                } else {
+                    // layer-1 bias as hi + mid + lo, each exact in bf16, summing to the fp32 bias
+                    const float b = args.wf[kOffB1 + n];
+                    const float h = __bfloat162float(__float2bfloat16_rn(b));
+                    const float m = __bfloat162float(__float2bfloat16_rn(b - h));
+                    v = __float2bfloat16_rn(k == 13 ? h : k == 14 ? m : (b - h) - m);
+                }
+            }
             else if (tile <= 5) v = args.wb[kOffW2 + (tile - 1) * 256 + k * kC + n];
             else if (tile <= 10) v = args.wb[kOffW3 + (tile - 6) * 256 + k * kC + n];
-            else if (tile == 11) { if (n < 5) v = args.wb[kOffW4 + n * kC + k]; }
-            else if (k < 3) {
-                // bias of layer tile - 12 as hi + mid + lo, each exact in bf16, summing to the fp32 bias
-                const float b = args.wf[(tile == 12 ? kOffB1 : tile == 13 ? kOffB2 : kOffB3) + n];
-                const float h = __bfloat162float(__float2bfloat16_rn(b));
-                const float m = __bfloat162float(__float2bfloat16_rn(b - h));
-                v = __float2bfloat16_rn(k == 0 ? h : k == 1 ? m : (b - h) - m);
-            }
+            else if (n < 5) v = args.wb[kOffW4 + n * kC + k];
             wt[tile * 256 + (k >> 3) * 128 + n * 8 + (k & 7)] = v;
-        }
-        // ones plane: rows of real positions carry 1.0 in channels 0 .. 2
-        uint32_t* ones = reinterpret_cast<uint32_t*>(smem + Lay::kOffOnes);
-        for (int i = tid; i < kTcRows * 4; i += kTcThreads) {
-            const int q = i >> 2, word = i & 3;
-            const bool real = !tc_pad_row(q);
-            ones[i] = !real ? 0u : word == 0 ? 0x3F803F80u : word == 1 ? 0x00003F80u : 0u;
         }
     } else {
         // tile = [2 chunks][16 n][16 k] e4m3: element (n, k) at (k / 16) * 256 + n * 16 + k % 16;
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) ar_score_tc_kernel(const TcArgs
             if (tc_pad_row(q)) continue;
             const SpinT* sp = spin + (m * 2) * kTcSpin + q;
             auto fv = [&](int k) -> uint32_t {          // operand code of feature k (compile-time k)
-                return feat_kind(k) == 2 ? 0u : (uint32_t)sp[feat_kind(k) * kTcSpin + feat_off(k)];
+                // BF16: 1.0 at k >= 13, where W1 holds the bias; E4M3: zero there
+                return feat_kind(k) == 2 ? (FP8 ? 0u : kPlus) : (uint32_t)sp[feat_kind(k) * kTcSpin + feat_off(k)];
             };
             const int r = kTcGuard + kTcRows * m + q;
             if constexpr (!FP8) {
@@ -347,14 +350,13 @@ __global__ void __launch_bounds__(kTcThreads, 4) ar_score_tc_kernel(const TcArgs
                     const uint32_t d = tmem + 16u * (uint32_t)m;
                     const uint64_t am = a0 + (uint64_t)(kTcRows * m);
                     if constexpr (!FP8) {
-                        if (layer < 3)     // bias: the ones plane times the layer's bias tile
-                            tc_mma<false>(d, smem_desc(s_base + Lay::kOffOnes, 0, 128), bt(12 + layer), 0u);
                         if (layer == 0 || layer == 3) {
-                            tc_mma<false>(d, am, bt(layer == 0 ? 0 : 11), layer == 0 ? 1u : 0u);
+                            tc_mma<false>(d, am, bt(layer == 0 ? 0 : 11), 0u);
                         } else {
 #pragma unroll
                             for (int t = 0; t < 5; ++t)
-                                tc_mma<false>(d, am + (uint64_t)(int64_t)tc_tap(t), bt(layer == 1 ? 1 + t : 6 + t), 1u);
+                                tc_mma<false>(d, am + (uint64_t)(int64_t)tc_tap(t), bt(layer == 1 ? 1 + t : 6 + t),
+                                              t > 0 ? 1u : 0u);
                         }
                     } else {
                         // e4m3: K = 32 takes two row offsets of one plane; the leading stride is their distance
@@ -380,6 +382,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) ar_score_tc_kernel(const TcArgs
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // ---- epilogue: this thread's row of every window of the chunk, kTcLdGroup windows per wait
             const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+            // the layer's bias (BF16 layer 1: already in the accumulator) and FP8 scale
+            float bl[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) bl[k] = (layer == 3 || (!FP8 && layer == 0)) ? 0.0f : bias[16 * layer + k];
+            const float sc = layer == 0 ? inv_s1 : layer == 1 ? inv_s2 : inv_s3;
             for (int m = 0; m < kTcWin; m += kTcLdGroup) {
                 float v[kTcLdGroup][16];
                 tc_ld64(tl + 16u * (uint32_t)m, v);
@@ -388,23 +395,25 @@ __global__ void __launch_bounds__(kTcThreads, 4) ar_score_tc_kernel(const TcArgs
                     const int r = kTcGuard + kTcRows * (m + h) + row;
                     if (layer < 3) {
                         if (pad) continue;       // pad rows are never written: they stay zero
+                        float x[16];
                         if constexpr (!FP8) {
-                            // the bias is in the accumulator: relu and bf16 rounding in one conversion
-                            *reinterpret_cast<uint4*>(act + r * 16) =
-                                make_uint4(tc_pack_bf16_relu(v[h][0], v[h][1]), tc_pack_bf16_relu(v[h][2], v[h][3]),
-                                           tc_pack_bf16_relu(v[h][4], v[h][5]), tc_pack_bf16_relu(v[h][6], v[h][7]));
-                            *reinterpret_cast<uint4*>(act + plane_bytes + r * 16) =
-                                make_uint4(tc_pack_bf16_relu(v[h][8], v[h][9]), tc_pack_bf16_relu(v[h][10], v[h][11]),
-                                           tc_pack_bf16_relu(v[h][12], v[h][13]), tc_pack_bf16_relu(v[h][14], v[h][15]));
-                        } else {
-                            const float* b = bias + 16 * layer;
-                            const float sc = layer == 0 ? inv_s1 : layer == 1 ? inv_s2 : inv_s3;
-                            float x[16];
+                            // bias add, then relu and bf16 rounding in one conversion
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) x[k] = fmaxf(v[h][k] * sc + b[k], 0.0f);
+                            for (int k = 0; k < 16; ++k) x[k] = v[h][k] + bl[k];
                             *reinterpret_cast<uint4*>(act + r * 16) =
-                                make_uint4(tc_pack_e4m3(x[0], x[1], x[2], x[3]), tc_pack_e4m3(x[4], x[5], x[6], x[7]),
-                                           tc_pack_e4m3(x[8], x[9], x[10], x[11]), tc_pack_e4m3(x[12], x[13], x[14], x[15]));
+                                make_uint4(tc_pack_bf16_relu(x[0], x[1]), tc_pack_bf16_relu(x[2], x[3]),
+                                           tc_pack_bf16_relu(x[4], x[5]), tc_pack_bf16_relu(x[6], x[7]));
+                            *reinterpret_cast<uint4*>(act + plane_bytes + r * 16) =
+                                make_uint4(tc_pack_bf16_relu(x[8], x[9]), tc_pack_bf16_relu(x[10], x[11]),
+                                           tc_pack_bf16_relu(x[12], x[13]), tc_pack_bf16_relu(x[14], x[15]));
+                        } else {
+                            // scale and bias, then relu and e4m3 rounding in one conversion
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) x[k] = v[h][k] * sc + bl[k];
+                            *reinterpret_cast<uint4*>(act + r * 16) =
+                                make_uint4(tc_pack_e4m3_relu(x[0], x[1], x[2], x[3]), tc_pack_e4m3_relu(x[4], x[5], x[6], x[7]),
+                                           tc_pack_e4m3_relu(x[8], x[9], x[10], x[11]),
+                                           tc_pack_e4m3_relu(x[12], x[13], x[14], x[15]));
                         }
                     } else {
                         // u[m][t][row] = H3[row] . W4[t] over the activations (no longer read)
