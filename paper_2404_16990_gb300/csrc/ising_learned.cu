@@ -628,10 +628,13 @@ __device__ __forceinline__ void load_b8(F wk, uint32_t (&b)[2]) {
 // (0, 1) and (2, 3), gathered by ldmatrix from per-window rings of 16-byte
 // rows (lanes 0-15 address the first tap's rows, lanes 16-31 the second's);
 // the (0, 0) tap is this step's own output, with a zero second half.  An
-// m16n8k32 accumulator fragment (channels 2tq, 2tq + 1 and 8 + 2tq, 9 + 2tq of
-// rows g, g + 8) is not the operand fragment the next layer needs (channels
-// 4tq .. 4tq + 3), so each layer's rounded output is regrouped by two warp
-// shuffles per row before its own-tap product and its stmatrix into the ring.
+// m16n8k32 accumulator fragment holds channels 2tq, 2tq + 1, 8 + 2tq, 9 + 2tq
+// of rows g, g + 8, while an operand fragment holds k = 4tq .. 4tq + 3.  The
+// hidden layers' channels are internal, so their operand order is permuted to
+// match (k = 4tq + e is channel chan_perm(k); the weight rows of layers 2-4
+// are permuted the same way): each lane's rounded accumulators are its operand
+// word as they stand, for the own-tap product and for the stmatrix into the
+// ring, with no exchange between lanes.
 // Accumulators start at bias x s_l (exact: s_l is a power of two) and are
 // scaled by 1 / s_l before relu and the e4m3 rounding, as (sum / s_l) + bias.
 // ---------------------------------------------------------------------------
@@ -648,25 +651,20 @@ __device__ __forceinline__ void stmatrix_x2(uint32_t addr, uint32_t r0, uint32_t
     asm volatile("stmatrix.sync.aligned.m8n8.x2.shared.b16 [%0], {%1, %2};\n" :: "r"(addr), "r"(r0), "r"(r1) : "memory");
 }
 
-// This lane's operand word (channels 4tq .. 4tq + 3 of a row) from the e4m3
-// pairs of the row's accumulator fragment across the lane's quad: p0 holds
-// channels (2tq, 2tq + 1), p1 channels (8 + 2tq, 9 + 2tq).
-__device__ __forceinline__ uint32_t regroup_e4m3(uint32_t p0, uint32_t p1, int lane) {
-    const uint32_t v = p0 | (p1 << 16);
-    const int tq = lane & 3, src = (lane & ~3) + 2 * (tq & 1), sh = (tq >> 1) * 16;
-    const uint32_t lo = __shfl_sync(0xffffffffu, v, src), hi = __shfl_sync(0xffffffffu, v, src + 1);
-    return ((lo >> sh) & 0xFFFFu) | (((hi >> sh) & 0xFFFFu) << 16);
-}
+// The hidden channel behind operand index k = 4tq + e: the accumulator
+// fragment's channels 2tq, 2tq + 1, 8 + 2tq, 9 + 2tq for e = 0 .. 3.
+__host__ __device__ constexpr int chan_perm(int k) { return 2 * (k >> 2) + (k & 1) + ((k & 2) ? 8 : 0); }
 
-// relu(d / s) rounded to e4m3 for the two n-tiles of a row pair, regrouped:
-// out[0] = row g, out[1] = row g + 8 (operand words of this lane)
-__device__ __forceinline__ void layer_out_e4m3(const float (&d)[2][4], float inv_s, int lane, uint32_t (&out)[2]) {
-    auto p = [&](float a, float b) -> uint32_t {
-        return __nv_cvt_float2_to_fp8x2(make_float2(fmaxf(a * inv_s, 0.0f), fmaxf(b * inv_s, 0.0f)), __NV_SATFINITE,
-                                        __NV_E4M3);
+// relu(d / s) rounded to e4m3 for the two n-tiles of a row pair: out[0] = row
+// g, out[1] = row g + 8, bytes in chan_perm order (operand words of this lane)
+__device__ __forceinline__ void layer_out_e4m3(const float (&d)[2][4], float inv_s, uint32_t (&out)[2]) {
+    auto p = [&](float a, float b) -> uint32_t {       // a in the low byte
+        uint16_t r;
+        asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(b * inv_s), "f"(a * inv_s));
+        return r;
     };
-    out[0] = regroup_e4m3(p(d[0][0], d[0][1]), p(d[1][0], d[1][1]), lane);
-    out[1] = regroup_e4m3(p(d[0][2], d[0][3]), p(d[1][2], d[1][3]), lane);
+    out[0] = p(d[0][0], d[0][1]) | (p(d[1][0], d[1][1]) << 16);
+    out[1] = p(d[0][2], d[0][3]) | (p(d[1][2], d[1][3]) << 16);
 }
 
 __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_fp8_kernel(const uint8_t* wq, const float* wscale,
@@ -691,16 +689,18 @@ __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_fp8_kernel(const 
 #pragma unroll
         for (int pr = 0; pr < 3; ++pr) {
             load_b8([&](int k, int nn) -> uint8_t {
-                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = k & 15;
+                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = chan_perm(k & 15);
                 return t >= 0 ? wq[kOffW2 + t * 256 + ci * kC + nt * 8 + nn] : 0;
             }, bq2[pr][nt]);
             load_b8([&](int k, int nn) -> uint8_t {
-                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = k & 15;
+                const int t = pr < 2 ? 2 * pr + (k >> 4) : (k < 16 ? 4 : -1), ci = chan_perm(k & 15);
                 return t >= 0 ? wq[kOffW3 + t * 256 + ci * kC + nt * 8 + nn] : 0;
             }, bq3[pr][nt]);
         }
     }
-    load_b8([&](int k, int nn) -> uint8_t { return (k < 16 && nn < 5) ? wq[kOffW4 + nn * kC + k] : 0; }, bq4);
+    load_b8([&](int k, int nn) -> uint8_t {
+        return (k < 16 && nn < 5) ? wq[kOffW4 + nn * kC + chan_perm(k)] : 0;
+    }, bq4);
     float bias_s[3][2][2];                         // bias x s_l: the accumulators' start
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_fp8_kernel(const 
                     d[nt][0] = d[nt][2] = bias_s[0][nt][0]; d[nt][1] = d[nt][3] = bias_s[0][nt][1];
                     mma16832_e4m3(d[nt], a, bq1[nt]);
                 }
-                layer_out_e4m3(d, inv_s[0], lane, h);
+                layer_out_e4m3(d, inv_s[0], h);
                 stmatrix_x2(ring_l + own * kRowQ, h[0], h[1]);
             }
             // ---- layers 2 and 3: the (0, 0) taps ----
@@ -806,13 +806,13 @@ __global__ void __launch_bounds__(kWarpsSmp * 32, 4) ar_sample_fp8_kernel(const 
                 const uint32_t a[4] = {h[0], h[1], 0u, 0u};
                 mma16832_e4m3(d2[0], a, bq2[2][0]); mma16832_e4m3(d2[1], a, bq2[2][1]);
             }
-            layer_out_e4m3(d2, inv_s[1], lane, h);
+            layer_out_e4m3(d2, inv_s[1], h);
             stmatrix_x2(ring_l + kL2 + own * kRowQ, h[0], h[1]);
             {
                 const uint32_t a[4] = {h[0], h[1], 0u, 0u};
                 mma16832_e4m3(d3[0], a, bq3[2][0]); mma16832_e4m3(d3[1], a, bq3[2][1]);
             }
-            layer_out_e4m3(d3, inv_s[2], lane, h);
+            layer_out_e4m3(d3, inv_s[2], h);
             // ---- layer 4: u[t] (unscaled) of rows g, g + 8 into the u ring ----
             {
                 const uint32_t a[4] = {h[0], h[1], 0u, 0u};
