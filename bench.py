@@ -28,6 +28,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 T_RUNS = (1.5, 2.269185, 3.0)
+L256_SEED = 2024   # seed of the 64-lattice 256^2 workload (simulations 0 .. 63)
 # algorithmic integer ops per site update: a quarter Philox4x32-10 block (15),
 # the accept decision (3), the bitsliced neighbour count (0.5)
 OPS_PER_SITE = 18.5
@@ -54,13 +55,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["l16384", "batch754"], default="l16384")
+    ap.add_argument("--workload", choices=["l16384", "batch754", "l256x64"], default="l16384")
     ap.add_argument("--L", type=int, default=16384)
-    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754)")
+    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754 and l256x64)")
     ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
     ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream", "persist", "cluster"],
                     default="tuned",
-                    help="batch754: force a plan instead of autotuning")
+                    help="batch754, l256x64: force a plan instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -196,6 +197,12 @@ def workload_config(args, rank: int = 0) -> dict:
                 "flips_per_step_per_gpu": 6 * L * L * n_sw,
                 "l2": f"flushed between timed steps; working set {6 * L * L // 8 / 2**20:g} MiB "
                       f"({'>' if 6 * L * L // 8 > 129e6 else '<'} 129 MB L2)"}
+    if args.workload == "l256x64":
+        return {"workload": f"64 lattices of 256x256 at T=2.269185 (the learned-proposal study's plain chain), "
+                            f"random starts (seed {L256_SEED + 1000 * rank}, simulations 0..63), {n_sw} sweeps "
+                            f"per step, one launch per step",
+                "lattices_per_gpu": 64, "L": 256, "sweeps_per_step": n_sw,
+                "flips_per_step_per_gpu": 64 * 256 * 256 * n_sw, "l2": "flushed between timed steps"}
     from paper_2404_16990_gb300 import workloads
     wl = workloads.batch754(master_seed=20240426 + rank)
     sites = sum(L * L for L in wl.Ls)
@@ -257,20 +264,26 @@ def cpu_baseline(L: int, seconds: float) -> dict:
     return cpu
 
 
-def time_oracle_batch754(rank: int = 0):
-    """One sweep of every lattice of the 754-lattice workload by the oracle,
-    lattices spread over the host threads."""
+def time_oracle_batch(workload: str, rank: int = 0):
+    """One sweep of every lattice of a batch workload (754 lattices, or 64 of
+    256^2) by the oracle, lattices spread over the host threads."""
     import oracle
     from paper_2404_16990_gb300 import workloads
     cores = os.cpu_count() or 1
-    wl = workloads.batch754(master_seed=20240426 + rank)
-    sig = [oracle.init(L, sd, i) for i, (L, sd) in enumerate(zip(wl.Ls, wl.seeds))]
+    if workload == "l256x64":
+        Ls, temps, seeds = [256] * 64, [T_RUNS[1]] * 64, [L256_SEED + 1000 * rank] * 64
+        what = "64 lattices of 256x256"
+    else:
+        wl = workloads.batch754(master_seed=20240426 + rank)
+        Ls, temps, seeds = wl.Ls, wl.temps, wl.seeds
+        what = "754 lattices"
+    sig = [oracle.init(L, sd, i) for i, (L, sd) in enumerate(zip(Ls, seeds))]
     t0 = time.perf_counter()
-    oracle.sweeps_batch(sig, wl.temps, wl.seeds, list(range(len(sig))), 0, 1, n_threads=cores)
+    oracle.sweeps_batch(sig, temps, seeds, list(range(len(sig))), 0, 1, n_threads=cores)
     secs = time.perf_counter() - t0
-    flips = sum(L * L for L in wl.Ls)
+    flips = sum(L * L for L in Ls)
     return {"value": flips / (secs * 1e9), "unit": "flip/ns", "cores": cores, "kind": "oracle",
-            "sample": "1 sweep of all 754 lattices (random starts), oracle on "
+            "sample": f"1 sweep of all {what} (random starts), oracle on "
                       f"{cores} host threads (one lattice per thread at a time)",
             "seconds": secs, "flips": flips}
 
@@ -285,7 +298,7 @@ def reference_arm(args):
             r = time_oracle(args.L, 0.0, max_sweeps=1)
             r["flips"] = args.L * args.L
         else:
-            r = time_oracle_batch754()
+            r = time_oracle_batch(args.workload)
         if i >= args.warmup:
             per_step.append(r)
     secs = sum(r["seconds"] for r in per_step)
@@ -369,6 +382,11 @@ def ours(args):
                 s = ising.IsingSim(Ls=[L] * 3, temps=list(T_RUNS), seeds=[seed] * 3, cold=cold,
                                    trace_cap=n_sw, stream=stream, device=dev)
                 sims.append(s)
+    elif args.workload == "l256x64":
+        n_sw = workload_sweeps(args)
+        with torch.cuda.stream(stream):
+            sims.append(ising.IsingSim(256, [T_RUNS[1]] * 64, L256_SEED + 1000 * rank, trace_cap=0, stream=stream,
+                                       device=dev))
     else:
         from paper_2404_16990_gb300 import workloads
         n_sw = workload_sweeps(args)
@@ -376,7 +394,7 @@ def ours(args):
         with torch.cuda.stream(stream):
             s = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=0, stream=stream, device=dev)
             sims.append(s)
-    if args.workload == "batch754" and args.plan != "tuned":
+    if args.workload != "l16384" and args.plan != "tuned":
         code = {"auto": ising.ISING_PLAN_AUTO, "resident": ising.ISING_PLAN_RESIDENT,
                 "stream": ising.ISING_PLAN_STREAM, "persist": ising.ISING_PLAN_PERSIST,
                 "cluster": ising.ISING_PLAN_CLUSTER}[args.plan]
@@ -384,9 +402,9 @@ def ours(args):
             s.set_plan(code)
     for s in sims:
         s.set_graph(True)
-    if args.workload != "batch754" or args.plan == "tuned":
-        if args.autotune or args.workload == "batch754":
-            tuned = [s.autotune(probe_sweeps=20 if args.workload == "batch754" else 5) for s in sims]
+    if args.workload == "l16384" or args.plan == "tuned":
+        if args.autotune or args.workload != "l16384":
+            tuned = [s.autotune(probe_sweeps=5 if args.workload == "l16384" else 20) for s in sims]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     sites = sum(sum(int(ising.ising_lattice_size(s.h, i)) ** 2 for i in range(s.n)) for s in sims)
     flips_per_step = sites * n_sw

@@ -44,6 +44,19 @@ def test_batch_workload_config():
     assert cfg["flips_per_step_per_gpu"] == cfg["spins_per_gpu"] * 10000
 
 
+def test_small_lattice_workload_reference_line():
+    """The 64-lattice 256^2 workload (the learned-proposal study's plain
+    chain): the reference arm sweeps all 64 lattices once per step."""
+    import argparse
+    import bench
+    cfg = bench.workload_config(argparse.Namespace(workload="l256x64", L=16384, sweeps=0))
+    assert cfg["lattices_per_gpu"] == 64 and cfg["L"] == 256 and cfg["sweeps_per_step"] == 10000
+    assert cfg["flips_per_step_per_gpu"] == 64 * 256 * 256 * 10000
+    line = _run("--impl", "reference", "--workload", "l256x64", "--steps", "1", "--warmup", "0")
+    assert line["config"] == cfg and line["value"] > 0
+    assert line["cpu_baseline"]["sample"].startswith("each step: 1 sweep of all 64 lattices of 256x256")
+
+
 def test_oracle_timing_on_one_thread():
     import bench
     r = bench.time_oracle(256, 0.0, threads=1)              # no time budget: one sweep
