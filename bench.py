@@ -58,10 +58,13 @@ def parse():
     ap.add_argument("--workload", choices=["l16384", "batch754", "l256x64"], default="l16384")
     ap.add_argument("--L", type=int, default=16384)
     ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 1000; 10000 for batch754 and l256x64)")
-    ap.add_argument("--autotune", action="store_true", help="autotune the plan before timing")
+    ap.add_argument("--autotune", action="store_true",
+                    help="(the default) autotune the plan before timing, outside the timed region")
+    ap.add_argument("--no-autotune", action="store_true", help="time the library's default plan instead")
     ap.add_argument("--plan", choices=["tuned", "auto", "resident", "stream", "persist", "cluster"],
                     default="tuned",
-                    help="batch754, l256x64: force a plan instead of autotuning")
+                    help="force a plan instead of autotuning")
+    ap.add_argument("--threads", type=int, default=0, help="with a forced plan: threads per block (0 = default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -394,17 +397,18 @@ def ours(args):
         with torch.cuda.stream(stream):
             s = ising.IsingSim(Ls=wl.Ls, temps=wl.temps, seeds=wl.seeds, trace_cap=0, stream=stream, device=dev)
             sims.append(s)
-    if args.workload != "l16384" and args.plan != "tuned":
+    if args.plan != "tuned":
         code = {"auto": ising.ISING_PLAN_AUTO, "resident": ising.ISING_PLAN_RESIDENT,
                 "stream": ising.ISING_PLAN_STREAM, "persist": ising.ISING_PLAN_PERSIST,
                 "cluster": ising.ISING_PLAN_CLUSTER}[args.plan]
         for s in sims:
-            s.set_plan(code)
+            s.set_plan(code, threads=args.threads)
     for s in sims:
         s.set_graph(True)
-    if args.workload == "l16384" or args.plan == "tuned":
-        if args.autotune or args.workload != "l16384":
-            tuned = [s.autotune(probe_sweeps=5 if args.workload == "l16384" else 20) for s in sims]
+    if args.plan == "tuned" and not args.no_autotune:
+        # the library's autotuner picks the plan (saves and restores the
+        # lattices and the sweep counter: no result changes)
+        tuned = [s.autotune(probe_sweeps=5 if args.workload == "l16384" else 20) for s in sims]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     sites = sum(sum(int(ising.ising_lattice_size(s.h, i)) ** 2 for i in range(s.n)) for s in sims)
     flips_per_step = sites * n_sw
@@ -507,10 +511,7 @@ def ours(args):
     if rank == 0:
         cfg = workload_config(args, rank)
         assert cfg["flips_per_step_per_gpu"] == flips_per_step
-        if args.workload == "l16384":
-            cfg.update({"kernel": "streaming half-sweep, CUDA graph", "plan": plan})
-        else:
-            cfg.update({"kernel": kname + ", CUDA graph", "plan": plan, "autotune_probe_flip_per_ns": tuned})
+        cfg.update({"kernel": kname + ", CUDA graph", "plan": plan, "autotune_probe_flip_per_ns": tuned})
         line = {
             "metric": "spin-flip attempts/ns", "value": value, "unit": "flip/ns", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
