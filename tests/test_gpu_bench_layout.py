@@ -3,11 +3,13 @@ benchmark times, against the CPU oracle bit for bit.
 
 * The 16384^2 configuration: two handles of three lattices (T = 1.5, 2.269185,
   3.0; one handle cold, one random from seed 2), the streaming plan forced to
-  4 words x 4 rows per thread, CUDA-graph replay of a 1000-sweep call with E/M
-  recorded every sweep.  Run in full at 2048^2 (all six lattices, 1000
-  sweeps, lattices and traces) and 4096^2 (all six on the GPU; the two cold
-  lattices at T = 1.5 and 3.0 in full against the oracle), and at the
-  benchmark's own 16384^2 on light-cone samples after 50 sweeps.
+  4 words x 4 rows per thread in blocks of 128 threads (the plan the
+  autotuner picks for the benchmark on GB300) or 256 (the library's default),
+  CUDA-graph replay of a 1000-sweep call with E/M recorded every sweep.  Run
+  in full at 2048^2 (all six lattices, 1000 sweeps, lattices and traces;
+  128 threads) and 4096^2 (all six on the GPU; the two cold lattices at
+  T = 1.5 and 3.0 in full against the oracle; 256 threads), and at the
+  benchmark's own 16384^2 on light-cone samples after 50 sweeps (both).
 * The 754-lattice batch (L in {128 .. 1024}, T in [1.8, 2.8], random
   starts): 100 sweeps of every lattice under the cooperative persistent plan
   the autotuner picks for it on GB300 (2 words x 8 rows per thread, 128
@@ -50,21 +52,22 @@ def site_from_words(words_t, L: int, y: int, x: int) -> int:
     return -1 if (w >> (j % 32)) & 1 else 1
 
 
-def bench_handles(L: int, n: int, seed: int = 2):
+def bench_handles(L: int, n: int, seed: int = 2, threads: int = 128):
     """The benchmark's two handles on one non-default stream, streaming plan
-    4 x 4, graph replay on, n sweeps each."""
+    4 x 4 with `threads` per block, graph replay on, n sweeps each."""
     import torch
     stream = torch.cuda.Stream()
     sims = []
     for cold in (True, False):
         s = ising.IsingSim(Ls=[L] * 3, temps=list(T_RUNS), seeds=[seed] * 3, cold=cold, trace_cap=n,
                            stream=stream)
-        s.set_plan(ising.ISING_PLAN_STREAM, words_per_thread=4, rows_per_item=4)
+        s.set_plan(ising.ISING_PLAN_STREAM, words_per_thread=4, rows_per_item=4, threads=threads)
         s.set_graph(True)
         sims.append(s)
     for s in sims:
         plan = ising.ising_get_plan(s.h)
-        assert (plan["plan"], plan["words_per_thread"], plan["rows_per_item"]) == (ising.ISING_PLAN_STREAM, 4, 4)
+        assert (plan["plan"], plan["words_per_thread"], plan["rows_per_item"], plan["threads"]) == \
+            (ising.ISING_PLAN_STREAM, 4, 4, threads)
     for s in sims:          # two calls: the graph of n/2 sweeps is captured, then replayed
         s.sweep(n // 2)
         s.sweep(n - n // 2)
@@ -73,7 +76,7 @@ def bench_handles(L: int, n: int, seed: int = 2):
 
 def test_bench_layout_2048_1000_sweeps_bit_exact():
     L, n, seed = 2048, 1000, 2
-    sims = bench_handles(L, n, seed)
+    sims = bench_handles(L, n, seed, threads=128)
     for h, cold in enumerate((True, False)):
         sim = sims[h]
         assert sim.sweeps_done == n
@@ -89,7 +92,7 @@ def test_bench_layout_4096_1000_sweeps_cold_lattices_bit_exact():
     """Config 2's cold starts at T = 1.5 and 3.0, 1000 sweeps, in the
     benchmark's layout (all six lattices swept on the GPU)."""
     L, n, seed = 4096, 1000, 2
-    sims = bench_handles(L, n, seed)
+    sims = bench_handles(L, n, seed, threads=256)
     cold = sims[0]
     Eg, Mg = cold.trace(n)
     for i in (0, 2):
@@ -105,11 +108,12 @@ def test_bench_layout_4096_1000_sweeps_cold_lattices_bit_exact():
             assert oracle.energy(s) == E[i] and int(s.sum(dtype=np.int64)) == M[i]
 
 
-def test_bench_layout_16384_light_cone_after_50_sweeps():
+@pytest.mark.parametrize("threads", [128, 256])
+def test_bench_layout_16384_light_cone_after_50_sweeps(threads):
     """The benchmark's own lattices: every one of the six sampled at 10
     sites (corners and edges included) after 50 graph-replayed sweeps."""
     L, n, seed = 16384, 50, 2
-    sims = bench_handles(L, n, seed)
+    sims = bench_handles(L, n, seed, threads=threads)
     rng = np.random.default_rng(50)
     for h, cold in enumerate((True, False)):
         for i, T in enumerate(T_RUNS):
