@@ -519,7 +519,8 @@ int create_common(ising_t* out, int n, const int* Ls, const double* temps, const
             e = launch_init_random(st, n, h->stream);
     }
     if (e == cudaSuccess && n > 0)
-        e = launch_observables(st, n, (const uint32_t*)(h->ws + lay.list), n, h->stream);
+        e = launch_observables(st, (uint32_t)*std::max_element(h->L.begin(), h->L.end()),
+                               (const uint32_t*)(h->ws + lay.list), n, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host buffers above go out of scope
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "create"));
     int rc = build_tables(h);
@@ -702,7 +703,8 @@ int ising_set_spins(ising_t h, int sim, const int8_t* in) {
         }
     CUDA_TRY(cudaMemcpyAsync(h->st.spins + h->layout.word_off[sim], w.data(), w.size() * 4, cudaMemcpyHostToDevice,
                              h->stream), "copy spins");
-    CUDA_TRY(launch_observables(h->st, h->n, (const uint32_t*)(h->ws + h->layout.list) + sim, 1, h->stream),
+    CUDA_TRY(launch_observables(h->st, (uint32_t)h->L[sim], (const uint32_t*)(h->ws + h->layout.list) + sim, 1,
+                                h->stream),
              "observables");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     return ISING_OK;
@@ -1062,7 +1064,7 @@ extern "C" int ising_random_stream(uint64_t seed, uint32_t s, uint32_t phase, ui
 namespace {
 
 constexpr int kSwTileSites = kSwTileW * kSwTileH;
-constexpr int kSwKernels = 7;   // local, merge, resolve, flip, observables (2), record
+constexpr int kSwKernels = 6;   // local, merge, resolve, flip, observables, record (with the E/M finish)
 
 struct SwLayout {
     size_t lat = 0, edges = 0, coins = 0, label = 0, total = 0;
@@ -1141,10 +1143,11 @@ int sw_prepare(ising_handle* h, void* scratch, size_t bytes, SwState* sw) {
 
 int enqueue_sw(ising_handle* h, const SwState& sw, int64_t n) {
     const uint32_t* list = (const uint32_t*)(h->ws + h->layout.list);
+    const uint32_t max_L = (uint32_t)*std::max_element(h->L.begin(), h->L.end());
     for (int64_t i = 0; i < n; ++i) {
         CUDA_TRY(launch_sw_clusters(h->st, sw, h->stream), "cluster labelling");
         CUDA_TRY(launch_sw_flip(h->st, sw, h->stream), "cluster flip");
-        CUDA_TRY(launch_observables(h->st, h->n, list, h->n, h->stream), "observables");
+        CUDA_TRY(launch_observables(h->st, max_L, list, h->n, h->stream, false), "observables");
         CUDA_TRY(launch_sw_record(h->st, h->n, h->stream), "record");
     }
     return ISING_OK;

@@ -423,12 +423,19 @@ __global__ void __launch_bounds__(256) sw_flip_kernel(DevState st, SwState sw) {
     base[((size_t)(ce ^ 1u) * L + y) * wn + k] ^= m_odd;
 }
 
-// E, M of the step (already in obs) into the trace and moments; then advance
-// the device sweep counter.  One block.
+// E, M of the step from the observables kernel's sums (aligned bonds, -1
+// spins; the sums are cleared) into obs, the trace and the moments; then
+// advance the device sweep counter.  One block.
 __global__ void sw_record_kernel(DevState st, int n_lat) {
     const unsigned long long t = st.ctl->t;
-    for (int lat = threadIdx.x; lat < n_lat; lat += blockDim.x)
-        record_em(st, (uint32_t)lat, st.lat[lat].L, st.obs[2 * lat], st.obs[2 * lat + 1], t);
+    for (int lat = threadIdx.x; lat < n_lat; lat += blockDim.x) {
+        const uint32_t L = st.lat[lat].L;
+        const long long N = (long long)L * L;
+        const unsigned long long sa = st.acc[2 * lat], sp = st.acc[2 * lat + 1];
+        st.acc[2 * lat] = 0;
+        st.acc[2 * lat + 1] = 0;
+        record_em(st, (uint32_t)lat, L, 2 * N - 2 * (long long)sa, N - 2 * (long long)sp, t);
+    }
     __syncthreads();
     if (threadIdx.x == 0) st.ctl->t = t + 1;
 }

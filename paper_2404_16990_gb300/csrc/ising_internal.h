@@ -125,8 +125,11 @@ struct SwState {
 
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_init_random(const DevState& st, int n_lat, cudaStream_t stream);
-cudaError_t launch_observables(const DevState& st, int n_lat, const uint32_t* lat_list,
-                               int n_list, cudaStream_t stream);
+// E, M of the listed lattices into obs; max_L = the largest listed side
+// (sizes the grid; 0: as for the largest lattices).  finalize = false leaves
+// the sums in acc for a kernel that turns them into E and M itself.
+cudaError_t launch_observables(const DevState& st, uint32_t max_L, const uint32_t* lat_list,
+                               int n_list, cudaStream_t stream, bool finalize = true);
 cudaError_t launch_resident(const DevState& st, int n_groups, int64_t n_sweeps,
                             int sweeps_per_unit, int threads, int grid, size_t smem_bytes,
                             cudaStream_t stream);

@@ -715,15 +715,22 @@ cudaError_t launch_init_random(const DevState& st, int n_lat, cudaStream_t strea
     return cudaGetLastError();
 }
 
-cudaError_t launch_observables(const DevState& st, int n_lat, const uint32_t* lat_list,
-                               int n_list, cudaStream_t stream) {
-    (void)n_lat;
+cudaError_t launch_observables(const DevState& st, uint32_t max_L, const uint32_t* lat_list,
+                               int n_list, cudaStream_t stream, bool finalize) {
     if (n_list <= 0) return cudaSuccess;
     const int sms = device_sm_count();
-    dim3 grid((unsigned)(n_list > 64 ? 4 : sms * 2), (unsigned)(n_list < 65535 ? n_list : 65535));
+    // blocks per lattice: enough for about four word pairs per thread of the
+    // largest listed lattice (L * L / 64 pairs), at most two per SM (four when
+    // more than 64 lattices share the grid)
+    uint32_t per_lat = (uint32_t)(n_list > 64 ? 4 : sms * 2);
+    if (max_L > 0) {
+        const uint64_t pairs = (uint64_t)max_L * (max_L / 64);
+        per_lat = (uint32_t)std::min<uint64_t>(per_lat, std::max<uint64_t>(1, (pairs + 1023) / 1024));
+    }
+    dim3 grid(per_lat, (unsigned)(n_list < 65535 ? n_list : 65535));
     observables_kernel<<<grid, 256, 0, stream>>>(st, lat_list, n_list);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !finalize) return e;
     observables_finalize_kernel<<<(n_list + 255) / 256, 256, 0, stream>>>(st, lat_list, n_list);
     return cudaGetLastError();
 }
