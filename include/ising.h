@@ -463,8 +463,9 @@ int ising_sweep_noalloc(uint32_t* dev_words, int n_lat, const int* Ls, const dou
 #define ISING_SW_MAX_L 32768
 
 /* Bytes of device scratch one cluster step of this handle needs: the
- * per-lattice table, 16 bytes per 64 x 16 tile, one coin bit and one 32-bit
- * label per site (about 4.14 bytes per site).  ISING_EINVAL if a lattice has
+ * per-lattice table and a 32-bit word per lattice, 16 bytes per 64 x 16
+ * tile, one coin bit and one 32-bit label per site (about 4.14 bytes per
+ * site).  ISING_EINVAL if a lattice has
  * L > ISING_SW_MAX_L. */
 int ising_sw_scratch_bytes(ising_t h, size_t* bytes);
 
@@ -498,11 +499,27 @@ int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes
  * With one draw per bond, each bond is tried at most once and the cluster is
  * the seed's connected component among equal spins joined by active bonds.
  * Scratch as for ising_sw_sweep (same size, same rules).  Asynchronous on the
- * handle's stream: one launch for all n steps of every lattice (a block per
- * lattice); after each step E and M are recorded exactly as after a sweep and
- * the sweep counter advances by one.  Steps, Swendsen-Wang steps and
- * Metropolis sweeps share the counter and may be mixed. */
+ * handle's stream; after each step E and M are recorded exactly as after a
+ * sweep and the sweep counter advances by one.  Steps, Swendsen-Wang steps
+ * and Metropolis sweeps share the counter and may be mixed.  Two ways to
+ * find the cluster, with the same result bit for bit (ising_wolff_set_method):
+ *   growth: one launch for all n steps of every lattice, a block per lattice
+ *     growing the cluster level by level -- fast when clusters are small
+ *     (above T_c), slow when one spans much of a large lattice;
+ *   labelling: the Swendsen-Wang step's labelling of all components of the
+ *     Wolff bonds over every SM, the seed's root looked up, and only that
+ *     component flipped (seven launches per step; graph replay as for
+ *     ising_sw_sweep) -- a fixed cost per site whatever the cluster's size.
+ * ISING_WOLFF_AUTO (the default) labels when some lattice of the handle is
+ * at T < 2.3, else grows. */
+#define ISING_WOLFF_AUTO 0
+#define ISING_WOLFF_GROWTH 1
+#define ISING_WOLFF_LABELS 2
 int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes);
+
+/* Choose how ising_wolff_sweep finds its clusters (ISING_WOLFF_AUTO, _GROWTH
+ * or _LABELS); ISING_EINVAL otherwise. */
+int ising_wolff_set_method(ising_t h, int method);
 
 /* Cluster labels of lattice `sim` for the step the handle would take next
  * (its current sweep counter), without taking it: host_labels[L*L]

@@ -148,6 +148,9 @@ struct ising_handle {
     std::vector<SwLat> sw_table;
     uint64_t sw_tiles = 0, sw_sites = 0;
     std::map<std::pair<int64_t, const void*>, cudaGraphExec_t> sw_graphs;
+    std::map<std::pair<int64_t, const void*>, cudaGraphExec_t> wolff_graphs;   // Wolff steps by labelling
+    int wolff_method = ISING_WOLFF_AUTO;
+    uint32_t* sw_seed_area = nullptr;    // seed roots in the last cluster scratch (set by sw_prepare)
 };
 
 namespace {
@@ -157,6 +160,8 @@ void drop_graphs(ising_handle* h) {
     h->graphs.clear();
     for (auto& kv : h->sw_graphs) cudaGraphExecDestroy(kv.second);
     h->sw_graphs.clear();
+    for (auto& kv : h->wolff_graphs) cudaGraphExecDestroy(kv.second);
+    h->wolff_graphs.clear();
 }
 
 int check_device_error(ising_handle* h) {
@@ -1067,7 +1072,7 @@ constexpr int kSwTileSites = kSwTileW * kSwTileH;
 constexpr int kSwKernels = 6;   // local, merge, resolve, flip, observables, record (with the E/M finish)
 
 struct SwLayout {
-    size_t lat = 0, edges = 0, coins = 0, label = 0, total = 0;
+    size_t lat = 0, edges = 0, coins = 0, label = 0, seeds = 0, total = 0;
 };
 
 // bond threshold floor(2^32 (1 - exp(-2/T))), at most 2^32 - 1
@@ -1114,6 +1119,7 @@ SwLayout sw_layout(const ising_handle* h) {
     l.edges = take((size_t)h->sw_tiles * sizeof(uint4));
     l.coins = take((size_t)(h->sw_sites / 32) * sizeof(uint32_t));
     l.label = take((size_t)h->sw_sites * sizeof(uint32_t));
+    l.seeds = take((size_t)h->n * sizeof(uint32_t));
     l.total = off;
     return l;
 }
@@ -1138,6 +1144,9 @@ int sw_prepare(ising_handle* h, void* scratch, size_t bytes, SwState* sw) {
     sw->edges = (uint4*)(base + l.edges);
     sw->coins = (uint32_t*)(base + l.coins);
     sw->label = (uint32_t*)(base + l.label);
+    sw->bond_phase = 7u;                     // Swendsen-Wang bonds; Wolff by labelling sets 10
+    sw->seed_root = nullptr;
+    h->sw_seed_area = (uint32_t*)(base + l.seeds);
     return ISING_OK;
 }
 
@@ -1208,6 +1217,34 @@ int ising_sw_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes
     return ISING_OK;
 }
 
+namespace {
+
+// Wolff steps by labelling: the Swendsen-Wang labelling of the Wolff bonds
+// (phase 10), the seed's root, the seed's component flipped; E and M from the
+// observables kernel, recorded as after a sweep.
+int enqueue_wolff_labels(ising_handle* h, const SwState& sw, int64_t n) {
+    const uint32_t* list = (const uint32_t*)(h->ws + h->layout.list);
+    const uint32_t max_L = (uint32_t)*std::max_element(h->L.begin(), h->L.end());
+    for (int64_t i = 0; i < n; ++i) {
+        CUDA_TRY(launch_wolff_clusters(h->st, sw, h->stream), "Wolff cluster labelling");
+        CUDA_TRY(launch_sw_flip(h->st, sw, h->stream), "Wolff cluster flip");
+        CUDA_TRY(launch_observables(h->st, max_L, list, h->n, h->stream, false), "observables");
+        CUDA_TRY(launch_sw_record(h->st, h->n, h->stream), "record");
+    }
+    return ISING_OK;
+}
+
+// The way ising_wolff_sweep runs: growth, or labelling (when some lattice is
+// at T < kWolffLabelsBelowT under the automatic choice).
+constexpr double kWolffLabelsBelowT = 2.3;
+bool wolff_by_labels(const ising_handle* h) {
+    if (h->wolff_method == ISING_WOLFF_LABELS) return true;
+    if (h->wolff_method == ISING_WOLFF_GROWTH) return false;
+    return *std::min_element(h->T.begin(), h->T.end()) < kWolffLabelsBelowT;
+}
+
+}  // namespace
+
 int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_bytes) {
     if (!h) return fail(ISING_EINVAL, "handle is NULL");
     if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
@@ -1217,8 +1254,37 @@ int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_by
     SwState sw{};
     int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
     if (rc != ISING_OK || n == 0) return rc;
-    // the visited bits (the coin region of the scratch) start at zero; each
-    // step clears the bits it set
+    if (wolff_by_labels(h)) {
+        sw.bond_phase = 10u;
+        sw.seed_root = h->sw_seed_area;
+        if (h->graph) {
+            if (h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");
+            const auto key = std::make_pair(n, (const void*)dev_scratch);
+            auto it = h->wolff_graphs.find(key);
+            if (it == h->wolff_graphs.end()) {
+                cudaGraph_t g = nullptr;
+                CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                rc = enqueue_wolff_labels(h, sw, n);
+                cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+                if (rc != ISING_OK) { if (g) cudaGraphDestroy(g); return rc; }
+                if (e != cudaSuccess) return cuda_fail(e, "end capture");
+                cudaGraphExec_t ex = nullptr;
+                e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+                it = h->wolff_graphs.emplace(key, ex).first;
+            }
+            CUDA_TRY(cudaGraphLaunch(it->second, h->stream), "graph launch");
+        } else {
+            rc = enqueue_wolff_labels(h, sw, n);
+            if (rc != ISING_OK) return rc;
+        }
+        h->t += n;
+        h->launches += 7 * n;
+        return ISING_OK;
+    }
+    // growth: the visited bits (the coin region of the scratch) start at
+    // zero; each step clears the bits it set
     CUDA_TRY(cudaMemsetAsync(sw.coins, 0, (size_t)(h->sw_sites / 8), h->stream), "clear visited bits");
     uint32_t max_small = 0;
     bool any_large = false;
@@ -1230,6 +1296,14 @@ int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_by
     CUDA_TRY(launch_advance_t(h->st, n, h->stream), "advance sweep counter");
     h->t += n;
     h->launches += 2;
+    return ISING_OK;
+}
+
+int ising_wolff_set_method(ising_t h, int method) {
+    if (!h) return fail(ISING_EINVAL, "handle is NULL");
+    if (method != ISING_WOLFF_AUTO && method != ISING_WOLFF_GROWTH && method != ISING_WOLFF_LABELS)
+        return fail(ISING_EINVAL, "unknown Wolff method %d", method);
+    h->wolff_method = method;
     return ISING_OK;
 }
 

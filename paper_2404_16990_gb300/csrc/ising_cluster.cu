@@ -48,7 +48,7 @@ static_assert(kTileW == 64 && kTileH <= 32 && kSwThreads % 32 == 0, "one 64-bit 
 constexpr int kWordsPerTile = kTileSites / 32;     // resolve: one thread per 32 sites
 constexpr int kPairsPerTile = kTileSites / 64;     // flip: one thread per 64 sites
 constexpr int kEdgeSites = kTileH + kTileW;        // merge: right edge rows + bottom edge columns
-constexpr uint32_t kPhaseBond = 7u, kPhaseCoin = 8u;
+constexpr uint32_t kPhaseBond = 7u, kPhaseCoin = 8u, kPhaseWolffSeed = 9u, kPhaseWolffBond = 10u;
 constexpr int kMaxChain = 1 << 26;                 // bound on one parent-pointer walk
 constexpr int kMaxRetry = 1 << 22;                 // bound on the retries of one union
 constexpr int kErrUnionBound = 3;                  // error word value
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kSwThreads) sw_local_kernel(DevState st, SwSta
         const uint64_t al_r = ~(row ^ ((row >> 1) | ((uint64_t)s_rbit[warp][k] << 63)));
         const uint64_t al_d = ~(row ^ below);
         const uint32_t p = (y0 + k) * L + x0 + xe;
-        const uint4 r = philox(p >> 1, t, d.sim, kPhaseBond, d.key0, d.key1);
+        const uint4 r = philox(p >> 1, t, d.sim, sw.bond_phase, d.key0, d.key1);
         const uint32_t vr = (uint32_t)(((al_r >> xe) & 1u) && r.x < d.thr) |
                             ((uint32_t)(((al_r >> xo) & 1u) && r.z < d.thr) << 1);
         const uint32_t vd = (uint32_t)(((al_d >> xe) & 1u) && r.y < d.thr) |
@@ -370,14 +370,34 @@ __global__ void __launch_bounds__(256) sw_resolve_kernel(DevState st, SwState sw
             continue;
         }
         if (f != r) lab[r] = f;
-        const uint4 v = philox(f >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
-        const uint32_t ln = f & 3u;
-        const uint32_t word = ln == 0 ? v.x : ln == 1 ? v.y : ln == 2 ? v.z : v.w;
-        if (word >> 31) atomicOr(&s_coin[warp][o], 1u << i);
+        bool flip;
+        if (sw.seed_root) {
+            flip = f == sw.seed_root[d.sim];           // Wolff: only the seed's cluster
+        } else {
+            const uint4 v = philox(f >> 2, t, d.sim, kPhaseCoin, d.key0, d.key1);
+            const uint32_t ln = f & 3u;
+            flip = ((ln == 0 ? v.x : ln == 1 ? v.y : ln == 2 ? v.z : v.w) >> 31) != 0;
+        }
+        if (flip) atomicOr(&s_coin[warp][o], 1u << i);
     }
     if (failed) atomicExch(&st.ctl->error, kErrUnionBound);
     __syncwarp();
     *coin_word = s_coin[warp][lane];
+}
+
+// Wolff by labelling: the seed of each lattice (phase 9, as the growth
+// kernel draws it) resolved to its final root.  One thread per lattice.
+__global__ void wolff_seed_kernel(DevState st, SwState sw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sw.n) return;
+    const SwLat d = sw.lat[i];
+    const uint32_t t = (uint32_t)st.ctl->t;
+    const uint32_t N = d.L * d.L;
+    const uint32_t r = philox(0u, t, d.sim, kPhaseWolffSeed, d.key0, d.key1).x;
+    const uint32_t p0 = (uint32_t)(((uint64_t)r * N) >> 32);
+    const uint32_t f = find_global(sw.label + d.site_off, p0);
+    if (f == ~0u) atomicExch(&st.ctl->error, kErrUnionBound);
+    sw.seed_root[d.sim] = f;
 }
 
 // Every site points at its final root (only for ising_sw_labels): the link
@@ -466,7 +486,6 @@ __global__ void sw_record_kernel(DevState st, int n_lat) {
 // ---------------------------------------------------------------------------
 constexpr int kWolffThreads = 512;
 constexpr uint32_t kWolffSmemMaxL = 256;
-constexpr uint32_t kPhaseWolffSeed = 9u, kPhaseWolffBond = 10u;
 
 template <bool SMEM>
 struct WolffStore {
@@ -619,6 +638,23 @@ cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream
     if (e != cudaSuccess) return e;
     const uint64_t edge_threads = (uint64_t)sw.total_tiles * kEdgeSites;
     sw_merge_kernel<<<(unsigned)((edge_threads + 255) / 256), 256, 0, stream>>>(st, sw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t words = (uint64_t)sw.total_tiles * kWordsPerTile;
+    sw_resolve_kernel<<<(unsigned)((words + 255) / 256), 256, 0, stream>>>(st, sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wolff_clusters(const DevState& st, const SwState& sw, cudaStream_t stream) {
+    if (sw.n <= 0 || sw.total_tiles == 0 || !sw.seed_root) return cudaErrorInvalidValue;
+    sw_local_kernel<<<(sw.total_tiles + kTilesPerBlock - 1) / kTilesPerBlock, kSwThreads, 0, stream>>>(st, sw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t edge_threads = (uint64_t)sw.total_tiles * kEdgeSites;
+    sw_merge_kernel<<<(unsigned)((edge_threads + 255) / 256), 256, 0, stream>>>(st, sw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wolff_seed_kernel<<<(sw.n + 127) / 128, 128, 0, stream>>>(st, sw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t words = (uint64_t)sw.total_tiles * kWordsPerTile;

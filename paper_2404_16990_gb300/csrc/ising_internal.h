@@ -121,6 +121,8 @@ struct SwState {
     uint4* edges;          // [tiles] right-edge bonds (x), bottom-edge bonds (z | w << 32)
     uint32_t* coins;       // [sites / 32] tile-local root mask, then each tile-local root's cluster coin
     uint32_t* label;       // [sites] parent pointers (site -> tile-local root -> cluster root)
+    uint32_t bond_phase;   // Philox phase of the bond draws: 7 Swendsen-Wang, 10 Wolff
+    uint32_t* seed_root;   // [n] Wolff by labelling: the final root of each lattice's seed, else null
 };
 
 // Launch wrappers (ising_kernels.cu).  All asynchronous on `stream`.
@@ -191,6 +193,12 @@ cudaError_t launch_sw_clusters(const DevState& st, const SwState& sw, cudaStream
 cudaError_t launch_sw_flip(const DevState& st, const SwState& sw, cudaStream_t stream);
 cudaError_t launch_sw_record(const DevState& st, int n_lat, cudaStream_t stream);
 cudaError_t launch_sw_compress(const SwState& sw, cudaStream_t stream);   // labels -> final roots
+// Wolff by labelling: after launch_sw_clusters' local and merge kernels have
+// linked the components of the Wolff bonds (bond_phase 10), each lattice's
+// seed (phase 9) is resolved to its final root into sw.seed_root, and the
+// resolve kernel sets "coin" 1 exactly for the tile-local roots of that
+// component.  One launch of the whole step: local, merge, seed, resolve.
+cudaError_t launch_wolff_clusters(const DevState& st, const SwState& sw, cudaStream_t stream);
 // Wolff single-cluster steps of every lattice (ising_cluster.cu); the scratch
 // of the cluster step serves as queue (labels) and visited bits (coins).
 // Lattices with L <= wolff_smem_max_L() run in shared memory (max_small_L =

@@ -145,6 +145,7 @@ def _load():
             "ising_sw_scratch_bytes": ([vp, ctypes.POINTER(sz)], ctypes.c_int),
             "ising_sw_get_thresholds": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "ising_sw_sweep": ([vp, i64, vp, sz], ctypes.c_int),
+            "ising_wolff_set_method": ([vp, ctypes.c_int], ctypes.c_int),
             "ising_wolff_sweep": ([vp, i64, vp, sz], ctypes.c_int),
             "ising_sw_labels": ([vp, ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         }
@@ -551,6 +552,13 @@ def ising_sw_get_thresholds(h) -> np.ndarray:
 
 def ising_sw_sweep(h, n: int, dev_scratch: int, nbytes: int) -> None:
     _check(_load().ising_sw_sweep(h, n, dev_scratch, nbytes))
+
+
+ISING_WOLFF_AUTO, ISING_WOLFF_GROWTH, ISING_WOLFF_LABELS = 0, 1, 2
+
+
+def ising_wolff_set_method(h, method: int) -> None:
+    _check(_load().ising_wolff_set_method(h, method))
 
 
 def ising_wolff_sweep(h, n: int, dev_scratch: int, nbytes: int) -> None:

@@ -206,13 +206,18 @@ def test_sw_errors():
 # --------------------------------------------------------------------------
 # Wolff single-cluster step
 # --------------------------------------------------------------------------
-def test_wolff_steps_bit_exact_uneven_batch():
+WOLFF_METHODS = [ising.ISING_WOLFF_GROWTH, ising.ISING_WOLFF_LABELS]
+
+
+@pytest.mark.parametrize("method", WOLFF_METHODS)
+def test_wolff_steps_bit_exact_uneven_batch(method):
     Ls = [64, 128, 64, 256, 192, 64, 320]
     temps = [TC, 1.5, 0.5, 3.0, TC, 1e3, 2.1]
     seeds = [21, 22, 23, 24, 25, 26, 27]
     n = 25
     for cold in (False, True):
         sim = ising.IsingSim(Ls=Ls, temps=temps, seeds=seeds, cold=cold, trace_cap=n)
+        ising.ising_wolff_set_method(sim.h, method)
         sim.wolff_sweep(n)
         Eg, Mg = sim.trace(n)
         for i, (L, T, sd) in enumerate(zip(Ls, temps, seeds)):
@@ -224,9 +229,11 @@ def test_wolff_steps_bit_exact_uneven_batch():
         sim.close()
 
 
-def test_wolff_mixed_with_sweeps_and_sw_steps():
+@pytest.mark.parametrize("method", WOLFF_METHODS + [ising.ISING_WOLFF_AUTO])
+def test_wolff_mixed_with_sweeps_and_sw_steps(method):
     L, T, seed = 256, TC, 78
     sim = ising.IsingSim(L, [T], seed, trace_cap=16)
+    ising.ising_wolff_set_method(sim.h, method)
     ref = oracle.init(L, seed, 0)
     t = 0
     for kind, k in (("mp", 2), ("wolff", 4), ("sw", 2), ("wolff", 3), ("mp", 1), ("wolff", 1)):
@@ -246,9 +253,11 @@ def test_wolff_mixed_with_sweeps_and_sw_steps():
     sim.close()
 
 
-def test_wolff_2048_at_tc_bit_exact():
+@pytest.mark.parametrize("method", WOLFF_METHODS)
+def test_wolff_2048_at_tc_bit_exact(method):
     L, T, seed, n = 2048, TC, 5, 6
     sim = ising.IsingSim(L, [T], seed, trace_cap=n)
+    ising.ising_wolff_set_method(sim.h, method)
     sim.sweep(20)
     ref = sim.spins(0)
     sim.wolff_sweep(n)
@@ -259,10 +268,12 @@ def test_wolff_2048_at_tc_bit_exact():
     assert C.max() > 1
 
 
-def test_wolff_limits():
+@pytest.mark.parametrize("method", WOLFF_METHODS)
+def test_wolff_limits(method):
     # T -> 0 from a cold start: the whole lattice every step; T -> inf: one site
     L = 128
     sim = ising.IsingSim(L, [0.01, 1e9], 3, cold=True, trace_cap=4)
+    ising.ising_wolff_set_method(sim.h, method)
     sim.wolff_sweep(4)
     E, M = sim.trace(4)
     assert list(M[0]) == [-(L * L), L * L, -(L * L), L * L]
@@ -273,8 +284,36 @@ def test_wolff_limits():
     sim.close()
 
 
+def test_wolff_labelling_at_4096_tc_and_graph_replay():
+    """One large lattice at T_c, where a cluster spans much of it: labelling
+    (all SMs) and growth (one block) give the same steps; graph replay of
+    the labelling path gives the same as direct launches."""
+    import torch
+    L, T, seed, n = 4096, TC, 12, 3
+    s = torch.cuda.Stream()
+    a = ising.IsingSim(L, [T], seed, trace_cap=n, stream=s)
+    b = ising.IsingSim(L, [T], seed, trace_cap=n, stream=s)
+    ising.ising_wolff_set_method(a.h, ising.ISING_WOLFF_LABELS)
+    ising.ising_wolff_set_method(b.h, ising.ISING_WOLFF_GROWTH)
+    a.set_graph(True)
+    a.wolff_sweep(1)
+    a.wolff_sweep(2)
+    b.wolff_sweep(3)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.spins(0), b.spins(0))
+    Ea, Ma = a.trace(n)
+    Eb, Mb = b.trace(n)
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ma, Mb)
+    assert np.abs(np.diff(Ma[0])).max() > 2                              # clusters of more than one site
+    a.close()
+    b.close()
+
+
 def test_wolff_scratch_errors():
     sim = ising.IsingSim(64, [TC], 1)
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_wolff_set_method(sim.h, 3)
+    assert e.value.code == ising.ISING_EINVAL
     with pytest.raises(ising.IsingError):
         ising.ising_wolff_sweep(sim.h, 1, 0, 0)          # no scratch
     with pytest.raises(ising.IsingError):
