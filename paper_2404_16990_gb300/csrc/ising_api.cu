@@ -1144,7 +1144,7 @@ int sw_prepare(ising_handle* h, void* scratch, size_t bytes, SwState* sw) {
     sw->edges = (uint4*)(base + l.edges);
     sw->coins = (uint32_t*)(base + l.coins);
     sw->label = (uint32_t*)(base + l.label);
-    sw->bond_phase = 7u;                     // Swendsen-Wang bonds; Wolff by labelling sets 10
+    sw->bond_phase = kSwBondPhase;           // Wolff by labelling sets kWolffBondPhase
     sw->seed_root = nullptr;
     h->sw_seed_area = (uint32_t*)(base + l.seeds);
     return ISING_OK;
@@ -1255,7 +1255,7 @@ int ising_wolff_sweep(ising_t h, int64_t n, void* dev_scratch, size_t scratch_by
     int rc = sw_prepare(h, dev_scratch, scratch_bytes, &sw);
     if (rc != ISING_OK || n == 0) return rc;
     if (wolff_by_labels(h)) {
-        sw.bond_phase = 10u;
+        sw.bond_phase = kWolffBondPhase;
         sw.seed_root = h->sw_seed_area;
         if (h->graph) {
             if (h->stream == nullptr) return fail(ISING_ESTATE, "graph replay needs a non-default stream");

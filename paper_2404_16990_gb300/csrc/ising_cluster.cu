@@ -48,7 +48,7 @@ static_assert(kTileW == 64 && kTileH <= 32 && kSwThreads % 32 == 0, "one 64-bit 
 constexpr int kWordsPerTile = kTileSites / 32;     // resolve: one thread per 32 sites
 constexpr int kPairsPerTile = kTileSites / 64;     // flip: one thread per 64 sites
 constexpr int kEdgeSites = kTileH + kTileW;        // merge: right edge rows + bottom edge columns
-constexpr uint32_t kPhaseBond = 7u, kPhaseCoin = 8u, kPhaseWolffSeed = 9u, kPhaseWolffBond = 10u;
+constexpr uint32_t kPhaseCoin = 8u, kPhaseWolffSeed = 9u, kPhaseWolffBond = kWolffBondPhase;
 constexpr int kMaxChain = 1 << 26;                 // bound on one parent-pointer walk
 constexpr int kMaxRetry = 1 << 22;                 // bound on the retries of one union
 constexpr int kErrUnionBound = 3;                  // error word value

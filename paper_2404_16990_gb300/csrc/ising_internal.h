@@ -103,6 +103,9 @@ constexpr int kSwTileW = 64;
 constexpr int kSwTileH = 16;
 constexpr int kSwThreads = 128;
 
+// Philox phases of the bond draws of a Swendsen-Wang step and of a Wolff step.
+constexpr uint32_t kSwBondPhase = 7u, kWolffBondPhase = 10u;
+
 // Per-lattice description (device, in the caller's SW scratch).
 struct SwLat {
     uint64_t word_off;     // first packed word of the lattice
@@ -121,7 +124,7 @@ struct SwState {
     uint4* edges;          // [tiles] right-edge bonds (x), bottom-edge bonds (z | w << 32)
     uint32_t* coins;       // [sites / 32] tile-local root mask, then each tile-local root's cluster coin
     uint32_t* label;       // [sites] parent pointers (site -> tile-local root -> cluster root)
-    uint32_t bond_phase;   // Philox phase of the bond draws: 7 Swendsen-Wang, 10 Wolff
+    uint32_t bond_phase;   // Philox phase of the bond draws: kSwBondPhase or kWolffBondPhase
     uint32_t* seed_root;   // [n] Wolff by labelling: the final root of each lattice's seed, else null
 };
 
